@@ -1,0 +1,78 @@
+"""A second, independent reader of the stream layouts, used by the tests.
+
+It walks the byte layout with Python integers (structure only: widths,
+records, counts and sizes) so that the oracle's encoder can be checked
+against the format definitions without trusting the oracle's own parser.
+Layouts: SIMD-BP128 metablocks (Sec. 6.2), the W32 variant, SIMD-FastPFOR
+pages (Sec. 5); readings R1-R16 are listed in the oracle's header.
+"""
+from __future__ import annotations
+
+import struct
+
+
+def le32(buf, off):
+    return struct.unpack_from("<I", bytes(buf[off:off + 4]))[0]
+
+
+def pad(x, a):
+    return (x + a - 1) // a * a
+
+
+def bp128_walk(buf, n, layout):
+    """Yields (offset, widths, size) per metablock; returns tail offset."""
+    buf = bytes(memoryview(buf))
+    nb = n // 128
+    metas = []
+    pos = 0
+    for m in range((nb + 15) // 16):
+        k = min(16, nb - 16 * m)
+        widths = list(buf[pos:pos + 16])
+        sb = sum(widths[:k])
+        size = 16 + 16 * sb if layout == 0 else 16 + 128 * ((4 * sb + 31) // 32)
+        metas.append((pos, widths, size, k))
+        pos += size
+    return metas, pos
+
+
+def fastpfor_walk(buf, n):
+    """Parses every page; returns (pages, tail offset).  A page is a dict with
+    the per-block records and the exception arrays' counts and offsets."""
+    buf = bytes(memoryview(buf))
+    nb = n // 128
+    pages = []
+    pos = 0
+    for p in range((nb + 511) // 512):
+        k = min(512, nb - 512 * p)
+        base = pos
+        len_at = 4 * le32(buf, base)
+        L = le32(buf, base + len_at)
+        rec_at = base + len_at + 4
+        records = []
+        r = 0
+        for _ in range(k):
+            b, mb = buf[rec_at + r], buf[rec_at + r + 1]
+            r += 2
+            pos_list = []
+            if mb > b:
+                c = buf[rec_at + r]
+                r += 1
+                pos_list = list(buf[rec_at + r:rec_at + r + c])
+                r += c
+            records.append((b, mb, pos_list))
+        assert r == L, (r, L)
+        q = rec_at + pad(L, 4)
+        bitset = le32(buf, q)
+        q += 4
+        arrays = {}
+        for d in range(1, 33):
+            if (bitset >> (d - 1)) & 1:
+                cnt = le32(buf, q)
+                q = base + pad(q + 4 - base, 16)
+                arrays[d] = (cnt, q)
+                q += 16 * d * ((cnt + 127) // 128)
+        end = base + pad(q - base, 16)
+        pages.append(dict(offset=base, blocks=k, len_at=len_at, byte_len=L, records=records,
+                          bitset=bitset, arrays=arrays, size=end - base))
+        pos = end
+    return pages, pos
