@@ -1,0 +1,179 @@
+/*
+ * icx -- GPU decoding of SIMD-BP128 / SIMD-FastPFOR integer streams with
+ * differential decoding, after Lemire & Boytsov, "Decoding billions of
+ * integers per second through vectorization" (arXiv 1209.2137).
+ *
+ * C ABI.  Every pointer named d_* is a device pointer (CUDA global memory) and
+ * every h_* a host pointer; sizes are counts of the stated unit.  The caller
+ * owns every buffer; no decode or encode call allocates memory.  Every call is
+ * asynchronous on `stream` unless stated otherwise.
+ *
+ * Errors.  Argument errors (null pointer, bad enum, misaligned pointer, n
+ * inconsistent with a size) are returned synchronously and nothing is
+ * launched.  Errors that depend on the data (a width byte above 32, a
+ * metablock or page that runs past in_bytes, an inconsistent FastPFOR page, a
+ * truncated Variable Byte tail, a device wait that gave up) are recorded in a
+ * status word inside the workspace; read it with icx_status_read after the
+ * stream has reached the call.  A decode that records an error leaves the
+ * affected outputs undefined but never reads or writes outside the buffers
+ * it was given.
+ *
+ * Stream formats (integers are uint32, stored little endian; n is never
+ * stored in a stream and is passed by the caller):
+ *
+ *  - SIMD-BP128 (Sec. 6.2): the n/128 full blocks of 128 integers are
+ *    grouped 16 per metablock; a metablock is a 16-byte descriptor whose
+ *    byte k is the bit width b_k of block k (unused bytes 0), followed by its
+ *    blocks, each 16*b_k bytes in the 4-lane vertical layout of Sec. 4
+ *    (Figs. 6-7: integer i of a block is field i/4 of lane i%4; word w of lane
+ *    l sits at byte 16*w + 4*l).  The n % 128 remaining integers follow the
+ *    last metablock in Variable Byte (Sec. 2.4: 7 bits per byte, low group
+ *    first, high bit set on the last byte of each integer).
+ *  - W32 (ICX_FMT_W32; not in the paper): the same descriptor, then the
+ *    metablock's payload as 32 lanes interleaved word by word (word w of lane
+ *    j at byte 128*w + 4*j).  Lane j = 4*g + l holds, block after block, the
+ *    integers 128*k + 16*g + 4*m + l (m = 0..3) at width b_k; every lane is
+ *    ceil(4*sum_k b_k / 32) words long.
+ *  - SIMD-FastPFOR (Sec. 5): pages of up to 512 blocks (65536 integers),
+ *    each page starting 16-byte aligned: a word giving the offset (in words)
+ *    of the byte-array length word, zero padding to byte 16, the blocks'
+ *    low b bits packed as above, the byte-array length (unpadded), the byte
+ *    array (per block b, maxbits and, when maxbits > b, the exception count
+ *    c and c positions; zero-padded to a multiple of 4), a 32-bit bitset whose
+ *    bit d-1 flags a non-empty exception array of width d, then for each such
+ *    d: its count, zero padding to 16 bytes, and its values packed at width d
+ *    in the same vertical layout, padded to a multiple of 128 values.  The
+ *    Variable Byte tail follows the last page.
+ *  - Differential coding (Sec. 3): ICX_DELTA_1 decodes x_i = delta_i +
+ *    x_{i-1}, ICX_DELTA_4 decodes x_i = delta_i + x_{i-4} (the vectorised
+ *    variant); values before the start count as 0, arithmetic is modulo 2^32,
+ *    and one chain runs over the whole array.
+ *
+ * An index (uint64 byte offsets of every metablock or page, plus the offset
+ * of the Variable Byte tail) gives the decoders random access to the
+ * metablocks; the paper's streams have no directory, so it is built once by
+ * bp128_index / fastpfor_index or written by the encoders.
+ */
+#ifndef ICX_H
+#define ICX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st *icx_stream_t;
+
+typedef enum {
+    ICX_OK = 0,
+    ICX_EINVAL = 1,   /* bad argument */
+    ICX_EALIGN = 2,   /* a device pointer is not 16-byte aligned */
+    ICX_ECORRUPT = 3, /* the stream does not follow the format */
+    ICX_ENOSPC = 4,   /* an output or workspace buffer is too small */
+    ICX_ECUDA = 5,    /* a CUDA runtime call failed */
+    ICX_ETIMEOUT = 6  /* a device-side wait gave up (no progress for ~2 s) */
+} icx_status;
+
+typedef enum { ICX_DELTA_NONE = 0, ICX_DELTA_1 = 1, ICX_DELTA_4 = 4 } icx_delta;
+typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1 } icx_layout;
+
+/* ------------------------------------------------------------- sizes ---- */
+
+/* Entries of a SIMD-BP128 index for n integers: ceil((n/128)/16) + 1. */
+size_t icx_bp128_index_len(size_t n);
+/* Entries of a SIMD-FastPFOR index for n integers: ceil((n/128)/512) + 1. */
+size_t icx_fastpfor_index_len(size_t n);
+/* Upper bound on the stream size in bytes. */
+size_t icx_bp128_max_bytes(size_t n, icx_layout fmt);
+size_t icx_fastpfor_max_bytes(size_t n);
+/* Bytes of device workspace a decode, delta_decode or index call on n
+ * integers needs (a 256-byte header plus look-back tile states). */
+size_t icx_workspace_bytes(size_t n);
+/* Bytes of device workspace an encode call on n integers needs. */
+size_t icx_encode_workspace_bytes(size_t n);
+
+/* Zero a workspace before its first use (asynchronous on `stream`).  A
+ * workspace resets itself at the end of every launch; one workspace must not
+ * be used by two launches that can run at the same time. */
+icx_status icx_workspace_init(void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
+
+/* Synchronises `stream`, copies the workspace's status word to *out and
+ * clears it.  Returns ICX_ECUDA if the copy fails, else ICX_OK. */
+icx_status icx_status_read(void *d_workspace, icx_stream_t stream, icx_status *out);
+
+/* ------------------------------------------------------------- index ---- */
+
+/* Walks the metablocks of a SIMD-BP128 (fmt = PAPER) or W32 stream and writes
+ * icx_bp128_index_len(n) byte offsets to d_index: entry m is the offset of
+ * metablock m, the last entry the offset of the Variable Byte tail (Sec. 6.2).
+ * The walk is sequential (each metablock's size comes from its descriptor). */
+icx_status bp128_index(const uint8_t *d_in, size_t in_bytes, size_t n, icx_layout fmt,
+                       uint64_t *d_index, void *d_workspace, size_t workspace_bytes,
+                       icx_stream_t stream);
+/* Same for the pages of a SIMD-FastPFOR stream (Sec. 5). */
+icx_status fastpfor_index(const uint8_t *d_in, size_t in_bytes, size_t n, uint64_t *d_index,
+                          void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
+
+/* ------------------------------------------------------------ decode ---- */
+
+/* Decodes n integers from the SIMD-BP128 (or W32) stream d_in[0..in_bytes)
+ * into d_out[0..n): bit unpacking (Sec. 4, Figs. 6-7), the Variable Byte
+ * tail (Sec. 2.4) and differential decoding (Sec. 3) in one pass.
+ * d_in and d_out must be 16-byte aligned; d_index is the stream's index
+ * (icx_bp128_index_len(n) entries) and may be NULL only when the stream holds
+ * at most one metablock (n < 17*128).
+ * d_workspace holds workspace_bytes >= icx_workspace_bytes(n) bytes and was
+ * initialised once with icx_workspace_init (else ICX_ENOSPC / undefined). */
+icx_status bp128_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, size_t n,
+                        icx_delta delta, icx_layout fmt, const uint64_t *d_index,
+                        void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
+
+/* Decodes n integers from the SIMD-FastPFOR stream d_in: per page the
+ * exception arrays, the packed low bits of every block, the patch
+ * out[p] |= high << b of every exception (Sec. 5), then differential
+ * decoding.  d_index may be NULL only when the stream holds at most one page
+ * (n < 513*128). */
+icx_status fastpfor_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, size_t n,
+                           icx_delta delta, const uint64_t *d_index, void *d_workspace,
+                           size_t workspace_bytes, icx_stream_t stream);
+
+/* Differential decoding alone (Sec. 3): d_out[i] = d_in[i] + d_out[i-s] for
+ * s = 1 or 4 (ICX_DELTA_NONE copies).  d_out may equal d_in (in place); the
+ * buffers must otherwise not overlap.  Both 16-byte aligned. */
+icx_status delta_decode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_delta delta,
+                        void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
+
+/* ------------------------------------------------------------ encode ---- */
+
+/* Differential coding (Sec. 3): d_out[i] = d_in[i] - d_in[i-s].  d_out must
+ * not overlap d_in. */
+icx_status delta_encode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_delta delta,
+                        icx_stream_t stream);
+
+/* Encodes d_x[0..n) as SIMD-BP128 / W32 (widths are the largest bit length of
+ * each block of deltas, Sec. 6.2) into d_out (capacity out_cap bytes, at
+ * least icx_bp128_max_bytes(n, fmt)), writes the index to d_index and the
+ * stream length in bytes to *d_out_bytes (device).  The bytes equal those of
+ * the format definition above, bit for bit. */
+icx_status bp128_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_layout fmt,
+                        uint8_t *d_out, size_t out_cap, uint64_t *d_index,
+                        uint64_t *d_out_bytes, void *d_encode_workspace,
+                        size_t encode_workspace_bytes, icx_stream_t stream);
+
+/* Encodes d_x[0..n) as SIMD-FastPFOR (per block the width minimising
+ * 128*b + c*(8 + maxbits - b), ties to the larger b; Sec. 5). */
+icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, uint8_t *d_out,
+                           size_t out_cap, uint64_t *d_index, uint64_t *d_out_bytes,
+                           void *d_encode_workspace, size_t encode_workspace_bytes,
+                           icx_stream_t stream);
+
+/* Library version string. */
+const char *icx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,184 @@
+// C ABI of the icx library (declared in include/icx.h): argument validation
+// and launches.  Argument errors return synchronously without launching;
+// data-dependent errors land in the workspace status word.
+#include <cstdint>
+#include <cstring>
+
+#include "icx_kernels.cuh"
+
+using icx::WsHeader;
+
+namespace {
+
+constexpr size_t kMaxN = (size_t)1 << 34;  // bound that keeps every size in range
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool valid_delta(int d) { return d == ICX_DELTA_NONE || d == ICX_DELTA_1 || d == ICX_DELTA_4; }
+bool valid_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_W32; }
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+icx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ICX_OK : ICX_ECUDA; }
+
+size_t metablocks(size_t n) { return (n / 128 + 15) / 16; }
+size_t pages(size_t n) { return (n / 128 + 511) / 512; }
+
+// encode workspace: header, then widths (1 byte per block), then sizes
+// (4 bytes per metablock or page, plus one).
+size_t enc_widths_off() { return icx::kWsHeaderBytes; }
+size_t enc_sizes_off(size_t n) { return enc_widths_off() + round_up(n / 128 + 1, 256); }
+
+}  // namespace
+
+extern "C" {
+
+size_t icx_bp128_index_len(size_t n) { return metablocks(n) + 1; }
+size_t icx_fastpfor_index_len(size_t n) { return pages(n) + 1; }
+
+size_t icx_bp128_max_bytes(size_t n, icx_layout fmt) {
+    const size_t M = metablocks(n), nb = n / 128;
+    const size_t body = fmt == ICX_FMT_W32 ? M * (16 + 128 * 64) : M * 16 + nb * 512;
+    return body + (n % 128) * 5 + 16;
+}
+
+size_t icx_fastpfor_max_bytes(size_t n) {
+    const size_t nb = n / 128, P = pages(n);
+    return P * (16 + 4 + 3 + 4 + 15 + 32 * (4 + 15 + 16 * 32)) + nb * (512 + 131 + 512) + (n % 128) * 5 + 16;
+}
+
+size_t icx_workspace_bytes(size_t n) {
+    const size_t tiles = n / 2048 + 16;
+    return round_up(icx::kWsHeaderBytes + tiles * icx::kStatesPerTile * sizeof(unsigned long long), 256);
+}
+
+size_t icx_encode_workspace_bytes(size_t n) {
+    const size_t sizes = round_up(4 * (metablocks(n) + pages(n) + 2), 256);
+    return enc_sizes_off(n) + sizes;
+}
+
+icx_status icx_workspace_init(void* d_ws, size_t ws_bytes, icx_stream_t stream) {
+    if (!d_ws || ws_bytes < icx::kWsHeaderBytes) return ICX_EINVAL;
+    return from_cuda(cudaMemsetAsync(d_ws, 0, ws_bytes, (cudaStream_t)stream));
+}
+
+icx_status icx_status_read(void* d_ws, icx_stream_t stream, icx_status* out) {
+    if (!d_ws || !out) return ICX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int v = 0;
+    WsHeader* h = static_cast<WsHeader*>(d_ws);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ICX_ECUDA;
+    if (cudaMemcpyAsync(&v, &h->status, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ICX_ECUDA;
+    if (cudaMemsetAsync(&h->status, 0, sizeof(v), s) != cudaSuccess) return ICX_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ICX_ECUDA;
+    *out = (icx_status)v;
+    return ICX_OK;
+}
+
+icx_status bp128_index(const uint8_t* d_in, size_t in_bytes, size_t n, icx_layout fmt, uint64_t* d_index,
+                       void* d_ws, size_t ws_bytes, icx_stream_t stream) {
+    if (!valid_fmt(fmt) || !d_index || !d_ws || n > kMaxN) return ICX_EINVAL;
+    if (metablocks(n) > 0 && !d_in) return ICX_EINVAL;
+    if (d_in && !aligned16(d_in)) return ICX_EALIGN;
+    if (ws_bytes < icx::kWsHeaderBytes) return ICX_ENOSPC;
+    return from_cuda(icx::launch_bp128_index(d_in, in_bytes, n, fmt, d_index, static_cast<WsHeader*>(d_ws),
+                                             (cudaStream_t)stream));
+}
+
+icx_status bp128_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, size_t n, icx_delta delta,
+                        icx_layout fmt, const uint64_t* d_index, void* d_ws, size_t ws_bytes,
+                        icx_stream_t stream) {
+    if (!valid_delta(delta) || !valid_fmt(fmt) || n > kMaxN) return ICX_EINVAL;
+    if (n == 0) return ICX_OK;
+    if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
+    if (!aligned16(d_in) || !aligned16(d_out) || (d_index && !aligned16(d_index))) return ICX_EALIGN;
+    if (ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
+    WsHeader* h = static_cast<WsHeader*>(d_ws);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!d_index) {
+        if (metablocks(n) > 1) return ICX_EINVAL;
+        const icx_status st = from_cuda(icx::launch_bp128_index(d_in, in_bytes, n, fmt, h->mini_index, h, s));
+        if (st != ICX_OK) return st;
+        d_index = h->mini_index;
+    }
+    return from_cuda(icx::launch_bp128_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s));
+}
+
+icx_status delta_decode(const uint32_t* d_in, uint32_t* d_out, size_t n, icx_delta delta, void* d_ws,
+                        size_t ws_bytes, icx_stream_t stream) {
+    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+    if (n == 0) return ICX_OK;
+    if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
+    if (!aligned16(d_in) || !aligned16(d_out)) return ICX_EALIGN;
+    if (d_in != d_out) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
+        if (a < b + 4 * n && b < a + 4 * n) return ICX_EINVAL;  // partial overlap
+    }
+    if (ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
+    return from_cuda(
+        icx::launch_delta_decode(delta, d_in, d_out, n, static_cast<WsHeader*>(d_ws), (cudaStream_t)stream));
+}
+
+icx_status delta_encode(const uint32_t* d_in, uint32_t* d_out, size_t n, icx_delta delta, icx_stream_t stream) {
+    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+    if (n == 0) return ICX_OK;
+    if (!d_in || !d_out) return ICX_EINVAL;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
+    if (a < b + 4 * n && b < a + 4 * n) return ICX_EINVAL;
+    return from_cuda(icx::launch_delta_encode(delta, d_in, d_out, n, (cudaStream_t)stream));
+}
+
+icx_status bp128_encode(const uint32_t* d_x, size_t n, icx_delta delta, icx_layout fmt, uint8_t* d_out,
+                        size_t out_cap, uint64_t* d_index, uint64_t* d_out_bytes, void* d_ews, size_t ews_bytes,
+                        icx_stream_t stream) {
+    if (!valid_delta(delta) || !valid_fmt(fmt) || n > kMaxN) return ICX_EINVAL;
+    if (!d_out || !d_index || !d_out_bytes || !d_ews || (n > 0 && !d_x)) return ICX_EINVAL;
+    if ((d_x && !aligned16(d_x)) || !aligned16(d_out)) return ICX_EALIGN;
+    if (out_cap < icx_bp128_max_bytes(n, fmt) || ews_bytes < icx_encode_workspace_bytes(n)) return ICX_ENOSPC;
+    uint8_t* base = static_cast<uint8_t*>(d_ews);
+    return from_cuda(icx::launch_bp128_encode(delta, fmt, d_x, n, d_out, d_index, d_out_bytes,
+                                              base + enc_widths_off(),
+                                              reinterpret_cast<uint32_t*>(base + enc_sizes_off(n)),
+                                              (cudaStream_t)stream));
+}
+
+icx_status fastpfor_index(const uint8_t* d_in, size_t in_bytes, size_t n, uint64_t* d_index, void* d_ws,
+                          size_t ws_bytes, icx_stream_t stream) {
+    if (!d_index || !d_ws || n > kMaxN) return ICX_EINVAL;
+    if (pages(n) > 0 && !d_in) return ICX_EINVAL;
+    if (d_in && !aligned16(d_in)) return ICX_EALIGN;
+    if (ws_bytes < icx::kWsHeaderBytes) return ICX_ENOSPC;
+    return from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, d_index, static_cast<WsHeader*>(d_ws),
+                                                (cudaStream_t)stream));
+}
+
+icx_status fastpfor_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, size_t n, icx_delta delta,
+                           const uint64_t* d_index, void* d_ws, size_t ws_bytes, icx_stream_t stream) {
+    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+    if (n == 0) return ICX_OK;
+    if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
+    if (!aligned16(d_in) || !aligned16(d_out) || (d_index && !aligned16(d_index))) return ICX_EALIGN;
+    if (ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
+    WsHeader* h = static_cast<WsHeader*>(d_ws);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!d_index) {
+        if (pages(n) > 1) return ICX_EINVAL;
+        const icx_status st = from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, h->mini_index, h, s));
+        if (st != ICX_OK) return st;
+        d_index = h->mini_index;
+    }
+    return from_cuda(icx::launch_fastpfor_decode(delta, d_in, in_bytes, d_out, n, d_index, h, s));
+}
+
+icx_status fastpfor_encode(const uint32_t* d_x, size_t n, icx_delta delta, uint8_t* d_out, size_t out_cap,
+                           uint64_t* d_index, uint64_t* d_out_bytes, void* d_ews, size_t ews_bytes,
+                           icx_stream_t stream) {
+    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+    if (!d_out || !d_index || !d_out_bytes || !d_ews || (n > 0 && !d_x)) return ICX_EINVAL;
+    if ((d_x && !aligned16(d_x)) || !aligned16(d_out)) return ICX_EALIGN;
+    if (out_cap < icx_fastpfor_max_bytes(n) || ews_bytes < icx_encode_workspace_bytes(n)) return ICX_ENOSPC;
+    return from_cuda(icx::launch_fastpfor_encode(delta, d_x, n, d_out, out_cap, d_index, d_out_bytes, d_ews,
+                                                 ews_bytes, (cudaStream_t)stream));
+}
+
+const char* icx_version(void) { return "icx 0.1 (sm_103a)"; }
+
+}  // extern "C"

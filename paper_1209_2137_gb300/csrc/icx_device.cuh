@@ -1,0 +1,327 @@
+// Device-side building blocks shared by the icx kernels: PTX wrappers for the
+// bulk-copy engine and mbarriers, warp scans, and the bounded single-pass
+// decoupled look-back that carries the running prefix sum of differential
+// decoding (Sec. 3) from one tile to the next.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "icx.h"
+
+namespace icx {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Workspace layout: a 256-byte header, then per look-back tile four 64-bit
+// states (one per residue mod 4; differential decoding with stride 1 uses the
+// first only).  A state holds (epoch << 2 | flag) in its high word and a
+// 32-bit sum in its low word; flag 1 = tile aggregate, 2 = inclusive prefix.
+// Any other high word (an older epoch, zero) means "not yet published".
+constexpr size_t kWsHeaderBytes = 256;
+constexpr int kStatesPerTile = 4;
+
+struct WsHeader {
+    unsigned int tile_counter;  // dynamic tile ids handed out by atomicAdd
+    unsigned int done_counter;  // CTAs that finished this launch
+    unsigned int epoch;         // launch number; tags the tile states
+    unsigned int status;        // first data-dependent error (icx_status)
+    uint64_t mini_index[2];  // index of a single-metablock/page stream
+    uint64_t total;          // encoders: stream length
+    unsigned int aux[48];
+};
+static_assert(sizeof(WsHeader) <= kWsHeaderBytes, "workspace header");
+
+// A device wait that sees no progress for this long gives up with ETIMEOUT.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long* tile_states(WsHeader* h) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h) + kWsHeaderBytes);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_error(WsHeader* h, unsigned code) {
+    atomicCAS(&h->status, 0u, code);
+}
+
+// ---------------------------------------------------------------- bulk copy
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later bulk-copy (async-proxy) accesses.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16); completion is signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// ------------------------------------------------------------- bit fields
+
+__device__ __forceinline__ uint32_t width_mask(uint32_t b) {
+    return b ? (0xFFFFFFFFu >> (32u - b)) : 0u;
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4& v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b) {
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ uint4 sub4(uint4 a, uint4 b) {
+    return make_uint4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+__device__ __forceinline__ uint4 shfl4(uint4 v, int src) {
+    return make_uint4(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src),
+                      __shfl_sync(FULL, v.z, src), __shfl_sync(FULL, v.w, src));
+}
+
+// ------------------------------------------------------------------ scans
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, v, off);
+        if (lane >= off) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint4 warp_incl_scan4(uint4 v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t a = __shfl_up_sync(FULL, v.x, off), b = __shfl_up_sync(FULL, v.y, off);
+        uint32_t c = __shfl_up_sync(FULL, v.z, off), d = __shfl_up_sync(FULL, v.w, off);
+        if (lane >= off) {
+            v.x += a;
+            v.y += b;
+            v.z += c;
+            v.w += d;
+        }
+    }
+    return v;
+}
+
+// Row ownership: lane t holds integers 4t..4t+3 of a 128-integer block.
+// Stride-1 prefix sum of the block plus the running carry (lane-uniform).
+__device__ __forceinline__ uint4 row_scan_d1(uint4 v, uint32_t& carry, int lane) {
+    v.y += v.x;
+    v.z += v.y;
+    v.w += v.z;
+    const uint32_t incl = warp_incl_scan(v.w, lane);
+    const uint32_t add = carry + incl - v.w;
+    carry += __shfl_sync(FULL, incl, 31);
+    return make_uint4(v.x + add, v.y + add, v.z + add, v.w + add);
+}
+
+// Row ownership, stride-4 prefix sum: component c of every lane belongs to
+// residue c, so the block is four column scans over the lanes.
+__device__ __forceinline__ uint4 row_scan_d4(uint4 v, uint4& carry, int lane) {
+    const uint4 incl = warp_incl_scan4(v, lane);
+    const uint4 out = add4(incl, carry);
+    carry = add4(carry, shfl4(incl, 31));
+    return out;
+}
+
+// Residue ownership: lane j = 4g + l holds integers 16g + 4m + l (m = 0..3)
+// in components m.  Stride-4 prefix sum: each residue l is a chain running
+// through m, then through the groups g; `carry` is the residue-l carry.
+__device__ __forceinline__ uint4 residue_scan_d4(uint4 v, uint32_t& carry, int lane) {
+    v.y += v.x;
+    v.z += v.y;
+    v.w += v.z;
+    uint32_t incl = v.w;
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const uint32_t add = carry + incl - v.w;
+    carry += __shfl_sync(FULL, incl, 28 + (lane & 3));
+    return make_uint4(v.x + add, v.y + add, v.z + add, v.w + add);
+}
+
+// Residue ownership -> row ownership: inside each group of four lanes the
+// 4x4 matrix M[m][l] (lane l holds column l) is transposed so lane l' holds
+// row l' = integers 16g + 4l' + 0..3.  Two butterfly exchanges.
+__device__ __forceinline__ uint4 residue_to_row(uint4 a, int lane) {
+    const int l = lane & 3;
+    const bool odd = l & 1;
+    // stage 1 (partner l^1): keep the rows of my parity, swap the others.
+    uint32_t keep0 = odd ? a.y : a.x;  // row p
+    uint32_t keep1 = odd ? a.w : a.z;  // row p + 2
+    uint32_t x0 = __shfl_xor_sync(FULL, odd ? a.x : a.y, 1);  // row p, column l^1
+    uint32_t x1 = __shfl_xor_sync(FULL, odd ? a.z : a.w, 1);  // row p+2, column l^1
+    // stage 2 (partner l^2): keep row l, send row l^2.
+    const bool hi = l & 2;
+    uint32_t own = hi ? keep1 : keep0;         // M[l][l]
+    uint32_t own_x = hi ? x1 : x0;             // M[l][l^1]
+    uint32_t y0 = __shfl_xor_sync(FULL, hi ? keep0 : keep1, 2);  // M[l][l^2]
+    uint32_t y1 = __shfl_xor_sync(FULL, hi ? x0 : x1, 2);        // M[l][l^3]
+    // e[c ^ l] = M[l][c]: undo the xor-by-l permutation.
+    uint32_t e0 = own, e1 = own_x, e2 = y0, e3 = y1;
+    if (odd) {
+        uint32_t t = e0; e0 = e1; e1 = t;
+        t = e2; e2 = e3; e3 = t;
+    }
+    if (hi) {
+        uint32_t t = e0; e0 = e2; e2 = t;
+        t = e1; e1 = e3; e3 = t;
+    }
+    return make_uint4(e0, e1, e2, e3);
+}
+
+// ------------------------------------------------------------- look-back
+
+// Decoupled look-back for tile `tile`, run by one full warp.  NL is the
+// number of independent chains (1 for stride 1, 4 for stride 4); agg holds
+// the tile's NL aggregates.  Returns the exclusive prefixes (components
+// 0..NL-1) and publishes the inclusive ones.  Every wait is bounded: after
+// kWaitLimitNs without progress the status word gets ICX_ETIMEOUT and the
+// tile publishes what it has, so no other tile can wait forever on it.
+template <int NL>
+__device__ uint4 lookback(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long* st = tile_states(h);
+    const uint32_t tagA = (epoch << 2) | 1u, tagP = (epoch << 2) | 2u;
+    const int c = lane % NL;
+    const uint32_t my_agg = comp(agg, c);
+    unsigned long long* mine = st + (size_t)tile * kStatesPerTile + c;
+    uint32_t excl = 0;
+    if (tile != 0) {
+        if (lane < NL) st_relaxed(mine, ((unsigned long long)tagA << 32) | my_agg);
+        const unsigned rmask = NL == 1 ? FULL : (0x11111111u << c);
+        long long end = tile;
+        bool done = false;
+        unsigned long long t0 = 0;
+        for (;;) {
+            const long long p = end - 1 - lane / NL;
+            uint32_t flag = 2, val = 0;
+            if (!done && p >= 0) {
+                const unsigned long long s = ld_relaxed(st + (size_t)p * kStatesPerTile + c);
+                const uint32_t hw = (uint32_t)(s >> 32);
+                val = (uint32_t)s;
+                flag = hw == tagP ? 2u : hw == tagA ? 1u : 0u;
+            }
+            const unsigned pm = __ballot_sync(FULL, flag == 2) & rmask;
+            const unsigned xm = __ballot_sync(FULL, flag == 0) & rmask;
+            const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 32u;
+            const unsigned upto = first >= 31 ? FULL : ((2u << first) - 1u);
+            const bool wait = (xm & upto) != 0;
+            if (__any_sync(FULL, wait)) {
+                if (t0 == 0) t0 = globaltimer();
+                if (globaltimer() - t0 > kWaitLimitNs) {
+                    if (lane == 0) set_error(h, ICX_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            t0 = 0;
+            uint32_t contrib = ((unsigned)lane <= first) ? val : 0u;
+#pragma unroll
+            for (int off = 16; off >= NL; off >>= 1) contrib += __shfl_xor_sync(FULL, contrib, off);
+            if (!done) excl += contrib;
+            if (first < 32) done = true;
+            if (__all_sync(FULL, done)) break;
+            end -= 32 / NL;
+        }
+    }
+    if (lane < NL) st_relaxed(mine, ((unsigned long long)tagP << 32) | (excl + my_agg));
+    uint4 r;
+    r.x = __shfl_sync(FULL, excl, 0);
+    r.y = NL > 1 ? __shfl_sync(FULL, excl, 1) : 0u;
+    r.z = NL > 1 ? __shfl_sync(FULL, excl, 2) : 0u;
+    r.w = NL > 1 ? __shfl_sync(FULL, excl, 3) : 0u;
+    return r;
+}
+
+// Epoch of this launch (constant while it runs).
+__device__ __forceinline__ uint32_t launch_epoch(WsHeader* h) {
+    return *reinterpret_cast<volatile unsigned int*>(&h->epoch);
+}
+
+// Called by every CTA after its last tile: the last CTA to finish resets the
+// tile counter and advances the epoch, so the next launch on the same
+// workspace starts clean without a memset.
+__device__ __forceinline__ void finish_launch(WsHeader* h, uint32_t epoch) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&h->done_counter, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&h->tile_counter, 0u);
+            atomicExch(&h->done_counter, 0u);
+            atomicExch(&h->epoch, (epoch + 1u) & 0x3FFFFFFFu);
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace icx

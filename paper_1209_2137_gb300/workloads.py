@@ -46,35 +46,40 @@ def uniform_u32(n: int, seed: int, bits: int = 32) -> np.ndarray:
     return _top_bits(splitmix64(seed, 0, n), bits).astype(np.uint32)
 
 
+def _sorted_distinct(values: np.ndarray) -> np.ndarray:
+    s = np.sort(values)
+    if s.size == 0:
+        return s
+    keep = np.empty(s.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
 def distinct_sorted(n: int, range_size: int, seed: int) -> np.ndarray:
     """n distinct values uniform in [0, range_size), sorted ascending.
 
-    Draws are taken in stream order and a value already drawn is redrawn
-    (rejection with a bitmap over the range)."""
+    Draws n plus a margin of candidates, removes duplicates, and if more than
+    n distinct values remain keeps the n whose keys from a second stream are
+    smallest (a uniformly random n-subset of a uniform set)."""
     if n > range_size:
         raise ValueError("more distinct values than the range holds")
-    seen = np.zeros(range_size, dtype=bool)
-    out = []
-    have, pos = 0, 0
-    while have < n:
-        need = n - have
-        batch = int(need * 1.25) + 1024
-        z = splitmix64(seed, pos, batch)
-        pos += batch
+    margin = max(1024, n // 8)
+    while True:
+        z = splitmix64(seed, 0, n + margin)
         if range_size & (range_size - 1) == 0:
             cand = _top_bits(z, int(math.log2(range_size)))
         else:
             cand = z % np.uint64(range_size)
-        cand = cand.astype(np.int64)
-        uniq, first = np.unique(cand, return_index=True)
-        fresh = ~seen[uniq]
-        uniq, first = uniq[fresh], first[fresh]
-        order = np.argsort(first, kind="stable")[:need]
-        take = uniq[order]
-        seen[take] = True
-        out.append(take)
-        have += take.size
-    return np.sort(np.concatenate(out)).astype(np.uint32)
+        u = _sorted_distinct(cand)
+        if u.size >= n:
+            break
+        margin *= 4
+    if u.size > n:
+        keys = splitmix64(seed ^ 0x2545F4914F6CDD1D, 0, u.size)
+        pick = np.sort(np.argpartition(keys, n - 1)[:n]) if n > 0 else np.zeros(0, dtype=np.int64)
+        u = u[pick]
+    return u.astype(np.uint32)
 
 
 def uniform_sorted(n: int, range_bits: int, seed: int) -> np.ndarray:
@@ -92,7 +97,7 @@ def clustered_sorted(centres: int = 1024, per_centre: int = 65536, window_bits: 
     off = _top_bits(z, window_bits).astype(np.int64) - (1 << (window_bits - 1))
     pts = np.repeat(c, per_centre) + off
     np.clip(pts, 0, (1 << range_bits) - 1, out=pts)
-    return np.unique(pts).astype(np.uint32)
+    return _sorted_distinct(pts).astype(np.uint32)
 
 
 def exception_heavy(n: int, seed: int = SEED_BASE + 3) -> np.ndarray:

@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI library: it builds for sm_103a, loads, and
+exports every function declared in include/icx.h; the pure size helpers agree
+with the format definitions.  No GPU needed."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1209_2137_gb300 import builder as b
+    b.build()
+    import paper_1209_2137_gb300 as icx
+    return icx.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "icx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z][a-z0-9_]*)\s*\(", text)) - {"defined"})
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 17
+    raw = ctypes.CDLL(os.path.join(ROOT, "paper_1209_2137_gb300", "libicx.so"))
+    for name in names:
+        assert hasattr(raw, name), name
+    import paper_1209_2137_gb300 as icx
+    assert set(icx.EXPORTED) <= set(names)
+
+
+def test_size_helpers_match_format(lib):
+    import paper_1209_2137_gb300 as icx
+    for n in [0, 1, 127, 128, 2047, 2048, 2049, 2176, 65536, 65537, 1 << 26, 56273636]:
+        assert icx.bp128_index_len(n) == oracle._load().orc_bp128_index_len(n)
+        assert icx.fastpfor_index_len(n) == oracle._load().orc_fastpfor_index_len(n)
+        assert icx.bp128_max_bytes(n, 0) >= oracle._load().orc_bp128_max_bytes(n) - 128 * ((n // 128 + 15) // 16)
+        assert icx.workspace_bytes(n) >= 256 + 32 * ((n // 128 + 15) // 16 + 2) // 8
+    assert icx.version().startswith("icx")
+
+
+def test_worst_case_streams_fit_max_bytes(lib):
+    import numpy as np
+    import paper_1209_2137_gb300 as icx
+    x = np.full(2048 * 3 + 100, 0xFFFFFFFF, dtype=np.uint32)
+    for fmt in (0, 1):
+        assert oracle.bp128_encode(x, 0, fmt).size <= icx.bp128_max_bytes(x.size, fmt)
+    assert oracle.fastpfor_encode(x, 0).size <= icx.fastpfor_max_bytes(x.size)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_1209_2137_gb300 as icx
+    monkeypatch.setattr(icx, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(icx, "_lib", None)
+    with pytest.raises(icx.IcxError):
+        icx.lib()
