@@ -1,0 +1,473 @@
+#!/usr/bin/env python3
+"""Decode throughput of the icx GPU library on the paper's long-array workload.
+
+One step = one pass of the whole decoding path over the synthetic workload:
+the 2^26-integer sorted uniform array and the clustered array (1,024 clusters,
+56.3 M integers after deduplication), each decoded as SIMD-BP128* (stride-4
+deltas), SIMD-BP128 (stride 1), W32* / W32 (the 32-lane layout) and
+SIMD-FastPFOR / SIMD-FastPFOR* -- twelve decodes.  Inputs (compressed
+streams + indexes, produced by the library's GPU encoders) are resident in
+HBM before timing.  Between decodes L2 is flushed by reading a buffer twice
+its size (untimed), so every decode starts cold and pays for its own
+write-backs; CUDA events bracket each decode on its stream.
+
+Prints one JSON line (see the keys below).  `--impl reference` times the
+scalar CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "decoded G ints/s"
+UNIT = "Gints/s"
+
+# (codec, delta, fmt, label) per array; a step decodes all of them on both arrays
+COMBOS = [
+    ("bp128", 4, 0, "SIMD-BP128*"),
+    ("bp128", 1, 0, "SIMD-BP128"),
+    ("bp128", 4, 1, "W32*"),
+    ("bp128", 1, 1, "W32"),
+    ("fastpfor", 1, 0, "SIMD-FastPFOR"),
+    ("fastpfor", 4, 0, "SIMD-FastPFOR*"),
+]
+KERNEL_NAMES = {"bp128": "bp128_decode_kernel", "fastpfor": "fastpfor_decode_kernel"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_arrays(n=None):
+    from paper_1209_2137_gb300 import workloads as W
+    t = time.time()
+    if n:  # reduced workload (profiling): the uniform array alone
+        arrays = {"uniform": W.uniform_sorted(n, 29, W.SEED_BASE + 2)}
+    else:
+        arrays = {"uniform": W.workload_uniform_long(), "clustered": W.workload_clustered_long()}
+    log(f"[bench] generated workload in {time.time() - t:.1f}s: "
+        + ", ".join(f"{k} n={v.size}" for k, v in arrays.items()))
+    return arrays
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 or ts > t1:
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- distributed --
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- traffic --
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1209_2137_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(label: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == label and parts[1] == src:
+                return float(parts[2]) * float(parts[3])  # bytes at capture size x scale to full size
+    return None
+
+
+# --------------------------------------------------------------- GPU arm --
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    icx.lib()  # fails loudly if the CUDA library is missing
+    arrays = workload_arrays(args.n)
+    stream = torch.cuda.current_stream()
+
+    # encode on the GPU (untimed) and verify one decode of each stream
+    streams = []
+    for name, x in arrays.items():
+        xt = torch.from_numpy(x).to(dev)
+        for codec, delta, fmt, label in COMBOS:
+            if codec == "fastpfor" and args.skip_fastpfor:
+                continue
+            enc = icx.bp128_encode(xt, delta, fmt) if codec == "bp128" else icx.fastpfor_encode(xt, delta)
+            streams.append(dict(array=name, codec=codec, delta=delta, fmt=fmt, label=label, enc=enc, n=x.size,
+                                x=xt))
+    nmax = max(s["n"] for s in streams)
+    out = torch.empty(nmax, dtype=torch.uint32, device=dev)
+    ws = icx.Workspace(nmax)
+    for s in streams:
+        o = out[: s["n"]]
+        icx.decode(s["enc"], out=o, workspace=ws)
+        ws.raise_status("verify decode")
+        if not torch.equal(o, s["x"]):
+            raise SystemExit(f"verification failed for {s['array']} {s['label']}")
+        s["bits_per_int"] = 8.0 * s["enc"].nbytes / s["n"]
+        s["alg_bytes"] = s["enc"].nbytes + 8 * s["enc"].index.numel() + 4 * s["n"]
+    log(f"[bench] {len(streams)} streams encoded on the GPU and verified")
+    for s in streams:
+        del s["x"]
+    torch.cuda.empty_cache()
+
+    props = torch.cuda.get_device_properties(dev)
+    l2 = getattr(props, "L2_cache_size", 132 * 1024 * 1024)
+    flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.int32, device=dev)
+    flush.fill_(1)
+
+    def flush_l2():
+        flush.sum(dtype=torch.int64)  # reads 2x L2 of clean lines
+
+    def decode(s):
+        icx.decode(s["enc"], out=out[: s["n"]], workspace=ws)
+
+    # warm-up
+    for _ in range(args.warmup):
+        for s in streams:
+            flush_l2()
+            decode(s)
+    torch.cuda.synchronize()
+
+    # timed: events bracket each decode only
+    K = args.steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in streams]
+          for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.time()
+        for k in range(K):
+            for i, s in enumerate(streams):
+                flush_l2()
+                ev[k][i][0].record(stream)
+                decode(s)
+                ev[k][i][1].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+    barrier(world)
+    per = np.array([[a.elapsed_time(b) for (a, b) in row] for row in ev])  # ms, [K, streams]
+    step_ms = per.sum(axis=1)
+    ms_per_step = float(np.mean(step_ms))
+    total_ms = max_over_ranks(float(step_ms.sum()), world)
+    ints_per_step = sum(s["n"] for s in streams)
+    value = world * ints_per_step * K / (total_ms / 1e3) / 1e9
+    launches_per_step = sum(1 if s["codec"] == "bp128" else 2 for s in streams)
+    ws.raise_status("timed decodes")
+
+    # roofline per stream and for the dominant one
+    peak, peak_kind = peaks()
+    kern = []
+    for i, s in enumerate(streams):
+        ms = float(np.mean(per[:, i]))
+        gbs = s["alg_bytes"] / (ms / 1e3) / 1e9
+        kern.append(dict(array=s["array"], codec=s["label"], n=s["n"], bits_per_int=round(s["bits_per_int"], 3),
+                         ms=round(ms, 4), gints_s=round(s["n"] / (ms / 1e3) / 1e9, 1), achieved_gbs=round(gbs, 1),
+                         frac=round(gbs / peak, 4)))
+    dom = max(range(len(streams)), key=lambda i: float(np.sum(per[:, i])))
+    ds = streams[dom]
+    dom_ms = float(np.mean(per[:, dom]))
+    achieved = ds["alg_bytes"] / (dom_ms / 1e3) / 1e9
+    traffic = recorded_traffic(f"{ds['array']}:{ds['label']}")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": f"{KERNEL_NAMES[ds['codec']]} ({ds['label']}, {ds['array']})",
+                "alg_bytes_per_launch": ds["alg_bytes"], "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"}
+    headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
+
+    e2e = run_e2e(args, streams, out, ws, dev, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(arrays, args)
+
+    clk = clocks.summary(t0, t1)
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded SplitMix64)",
+        "config": {
+            "workload": workload_label(arrays, streams),
+            "ints_per_step": ints_per_step, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "flushed between decodes (untimed read of 2x L2), events bracket each decode",
+            "streams": kern,
+        },
+        "roofline": roofline,
+        "headline_kernel": kern[headline],
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * K,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def workload_label(arrays, streams):
+    parts = []
+    for name, x in arrays.items():
+        parts.append(f"{name} n={x.size}" + (" (2^26 in [0,2^29))" if name == "uniform" and x.size == 1 << 26
+                                               else " (1024 clusters, 2^18 windows)" if name == "clustered" else ""))
+    labels = sorted({s["label"] for s in streams}, key=lambda l: [c[3] for c in COMBOS].index(l))
+    return (f"long sorted uint32 arrays, {len(streams)} decodes per step: {{" + "; ".join(parts) + "} x {"
+            + ", ".join(labels) + "}")
+
+
+def run_e2e(args, streams, out, ws, dev, world):
+    """Same metric through the public API with host buffers: every step copies
+    each stream and its index from pinned host memory, decodes, and copies the
+    integers back to pinned host memory."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+
+    steps = max(3, min(args.steps, args.e2e_steps))
+    host = []
+    for s in streams:
+        hd = torch.empty(s["enc"].nbytes, dtype=torch.uint8, pin_memory=True)
+        hd.copy_(s["enc"].data)
+        hi = torch.empty(s["enc"].index.numel(), dtype=torch.uint64, pin_memory=True)
+        hi.copy_(s["enc"].index)
+        dd = torch.empty_like(s["enc"].data)
+        di = torch.empty_like(s["enc"].index)
+        host.append((hd, hi, dd, di))
+    hout = torch.empty(out.numel(), dtype=torch.uint32, pin_memory=True)
+    h2d = sum(h[0].numel() + 8 * h[1].numel() for h in host)
+    d2h = sum(4 * s["n"] for s in streams)
+
+    def step():
+        for s, (hd, hi, dd, di) in zip(streams, host):
+            dd.copy_(hd, non_blocking=True)
+            di.copy_(hi, non_blocking=True)
+            enc = icx.Encoded(dd, di, s["n"], s["codec"], s["delta"], s["fmt"])
+            icx.decode(enc, out=out[: s["n"]], workspace=ws)
+            hout[: s["n"]].copy_(out[: s["n"]], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(a.elapsed_time(b), world)
+    ints = sum(s["n"] for s in streams) * steps * world
+    return {"value": round(ints / (ms / 1e3) / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+# --------------------------------------------------------- CPU baseline --
+
+def oracle_streams(arrays, prefix):
+    import oracle
+    out = []
+    for name, x in arrays.items():
+        xs = x[:prefix]
+        for codec, delta, fmt, label in COMBOS:
+            out.append((codec, delta, fmt, label, oracle.encode(codec, xs, delta, fmt), xs.size))
+    return out
+
+
+def cpu_baseline(arrays, args):
+    """The oracle decoder as it stands (single thread) on a bounded sample."""
+    import oracle
+    prefix = args.cpu_prefix
+    enc = oracle_streams(arrays, prefix)
+    t = time.perf_counter()
+    ints = 0
+    for codec, delta, fmt, label, data, n in enc:
+        oracle.decode(codec, data, n, delta, fmt)
+        ints += n
+    dt = time.perf_counter() - t
+    return {"value": round(ints / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {prefix} integers of each array, all 12 decodes ({ints} ints, {dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the scalar CPU oracle, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    arrays = workload_arrays(args.n)
+    # size the per-step sample so the whole run stays within ~2 minutes
+    calib = oracle_streams({k: v[: 1 << 16] for k, v in arrays.items()}, 1 << 16)
+    t = time.perf_counter()
+    for codec, delta, fmt, label, data, n in calib:
+        oracle.decode(codec, data, n, delta, fmt)
+    rate = sum(c[-1] for c in calib) / (time.perf_counter() - t)
+    budget = 100.0 / max(1, args.steps + args.warmup)
+    prefix = int(min(1 << 26, max(2048, rate * budget / len(calib)))) // 2048 * 2048
+    enc = oracle_streams(arrays, prefix)
+    for _ in range(args.warmup):
+        for codec, delta, fmt, label, data, n in enc:
+            oracle.decode(codec, data, n, delta, fmt)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for codec, delta, fmt, label, data, n in enc:
+            oracle.decode(codec, data, n, delta, fmt)
+    dt = time.perf_counter() - t
+    ints = sum(e[-1] for e in enc) * args.steps
+    value = ints / dt / 1e9
+    sample = f"first {prefix} integers of each array per step, all 12 decodes"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded SplitMix64)",
+        "config": {"workload": "long sorted uint32 arrays (sample), 12 decodes per step",
+                   "parallelism": "single CPU thread"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["icx", "reference"], default="icx")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-prefix", type=int, default=1 << 24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fastpfor", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

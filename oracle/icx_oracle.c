@@ -473,7 +473,7 @@ static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_c
         if (maxbits > b) {
             if (r + 1 > L) return 0;
             size_t c = bytes[r++];
-            if (r + c > L) return 0;
+            if (c > 128 || r + c > L) return 0; /* a block has 128 values */
             int dd = maxbits - b;
             if (cursor[dd] + c > arr_n[dd]) return 0;
             for (size_t e = 0; e < c; ++e) {

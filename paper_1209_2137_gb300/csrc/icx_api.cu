@@ -45,14 +45,12 @@ size_t icx_fastpfor_max_bytes(size_t n) {
     return P * (16 + 4 + 3 + 4 + 15 + 32 * (4 + 15 + 16 * 32)) + nb * (512 + 131 + 512) + (n % 128) * 5 + 16;
 }
 
-size_t icx_workspace_bytes(size_t n) {
-    const size_t tiles = n / 2048 + 16;
-    return round_up(icx::kWsHeaderBytes + tiles * icx::kStatesPerTile * sizeof(unsigned long long), 256);
-}
+size_t icx_workspace_bytes(size_t n) { return icx::ws_total_bytes(n); }
 
 size_t icx_encode_workspace_bytes(size_t n) {
-    const size_t sizes = round_up(4 * (metablocks(n) + pages(n) + 2), 256);
-    return enc_sizes_off(n) + sizes;
+    const size_t bp = enc_sizes_off(n) + round_up(4 * (metablocks(n) + 2), 256);
+    const size_t fp = icx::fastpfor_encode_workspace_bytes(n);
+    return bp > fp ? bp : fp;
 }
 
 icx_status icx_workspace_init(void* d_ws, size_t ws_bytes, icx_stream_t stream) {
@@ -89,7 +87,8 @@ icx_status bp128_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, s
     if (!valid_delta(delta) || !valid_fmt(fmt) || n > kMaxN) return ICX_EINVAL;
     if (n == 0) return ICX_OK;
     if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
-    if (!aligned16(d_in) || !aligned16(d_out) || (d_index && !aligned16(d_index))) return ICX_EALIGN;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws) || (d_index && !aligned16(d_index)))
+        return ICX_EALIGN;
     if (ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
     WsHeader* h = static_cast<WsHeader*>(d_ws);
     cudaStream_t s = (cudaStream_t)stream;
@@ -155,7 +154,8 @@ icx_status fastpfor_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out
     if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
     if (n == 0) return ICX_OK;
     if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
-    if (!aligned16(d_in) || !aligned16(d_out) || (d_index && !aligned16(d_index))) return ICX_EALIGN;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws) || (d_index && !aligned16(d_index)))
+        return ICX_EALIGN;
     if (ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
     WsHeader* h = static_cast<WsHeader*>(d_ws);
     cudaStream_t s = (cudaStream_t)stream;

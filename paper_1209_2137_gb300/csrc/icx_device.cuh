@@ -32,6 +32,31 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) <= kWsHeaderBytes, "workspace header");
 
+// Workspace regions after the header: look-back tile states, then (for
+// SIMD-FastPFOR) one 16-byte record per block and one 144-byte record per page
+// written by the page parse and read by the decode.
+struct BlockMeta {
+    uint32_t packed_off;  // page-relative byte offset of the block's packed low bits
+    uint32_t pos_off;     // page-relative byte offset of its exception positions
+    uint32_t cursor;      // index of its first exception in array d
+    uint8_t b, d, c, flags;
+};
+static_assert(sizeof(BlockMeta) == 16, "block meta");
+constexpr size_t kPageMetaWords = 36;  // arr_off[32] (page-relative), bad flag, pad
+
+__host__ __device__ inline size_t ws_tiles(size_t n) { return n / 2048 + 16; }
+__host__ __device__ inline size_t ws_blockmeta_off(size_t n) { return kWsHeaderBytes + 32 * ws_tiles(n); }
+__host__ __device__ inline size_t ws_pagemeta_off(size_t n) { return ws_blockmeta_off(n) + 16 * (n / 128 + 1); }
+__host__ __device__ inline size_t ws_unitmeta_off(size_t n) {
+    const size_t end = ws_pagemeta_off(n) + 4 * kPageMetaWords * ((n / 128 + 511) / 512 + 1);
+    return (end + 255) / 256 * 256;
+}
+// per unit of 16 blocks: page-relative offset and size of its packed low bits
+__host__ __device__ inline size_t ws_total_bytes(size_t n) {
+    const size_t end = ws_unitmeta_off(n) + 8 * (n / 2048 + 2);
+    return (end + 255) / 256 * 256;
+}
+
 // A device wait that sees no progress for this long gives up with ETIMEOUT.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 

@@ -1,18 +1,463 @@
-// SIMD-FastPFOR (Sec. 5): page walk, decoding and encoding.
+// SIMD-FastPFOR decoding (Sec. 5, SIMD variant): page walk, page parse and
+// the fused unpack + exception patch + differential decoding.
+//
+// The byte array of a page (per block b, maxbits and, for blocks with
+// exceptions, the count c and c positions) has variable-length records, so
+// finding block k's record needs the records before it.  The decode is
+// therefore two launches:
+//  1. fastpfor_meta_kernel -- one warp per page walks the byte array through
+//     a shared-memory window and writes a fixed 16-byte record per block
+//     (packed offset, positions offset, exception cursor, b, d, c) plus the
+//     page-relative offsets of the 32 exception arrays;
+//  2. fastpfor_decode_kernel -- units of 16 blocks exactly like the
+//     SIMD-BP128 decoder: one bulk copy of the unit's packed low bits into
+//     shared memory, vertical unpacking, then every exception of the unit is
+//     fetched by random access into its vertically packed array (element q:
+//     chunk q/128, lane q%4, field (q%128)/4) and OR-ed in as high << b
+//     (Sec. 5 "patching"), then the tile epilogue (scan, look-back, stores).
 #include "icx_kernels.cuh"
+#include "icx_tile.cuh"
 
 namespace icx {
 
-cudaError_t launch_fastpfor_decode(int, const uint8_t*, size_t, uint32_t*, size_t, const uint64_t*, WsHeader*,
-                                   cudaStream_t) {
-    return cudaErrorNotSupported;
+constexpr uint32_t kBlocksPerPage = 512;
+constexpr uint32_t kUnitsPerPage = kBlocksPerPage / 16;
+
+__device__ __forceinline__ uint32_t ld32(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
+__host__ __device__ __forceinline__ size_t pad_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------- page walk
+
+// Sequential walk over the pages: each page's size follows from its header
+// word, byte-array length, bitset and exception counts.
+__global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n,
+                                      uint64_t* __restrict__ index, WsHeader* h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
+    size_t pos = 0;
+    bool bad = false;
+    for (size_t p = 0; p < P; ++p) {
+        index[p] = pos;
+        if (bad) continue;
+        if (pos + 16 > in_bytes) {
+            bad = true;
+            continue;
+        }
+        const size_t len_at = 4 * (size_t)ld32(in + pos);
+        if (len_at < 16 || (len_at & 15) || pos + len_at + 4 > in_bytes) {
+            bad = true;
+            continue;
+        }
+        const size_t L = ld32(in + pos + len_at);
+        size_t q = pos + len_at + 4 + pad_up(L, 4);
+        if (q + 4 > in_bytes) {
+            bad = true;
+            continue;
+        }
+        const uint32_t bitset = ld32(in + q);
+        q += 4;
+        for (int d = 1; d <= 32 && !bad; ++d) {
+            if (!((bitset >> (d - 1)) & 1u)) continue;
+            if (q + 4 > in_bytes) {
+                bad = true;
+                break;
+            }
+            const size_t cnt = ld32(in + q);
+            q = pos + pad_up(q + 4 - pos, 16) + 16 * (size_t)d * ((cnt + 127) / 128);
+            if (q > in_bytes) bad = true;
+        }
+        const size_t end = pos + pad_up(q - pos, 16);
+        if (end > in_bytes) bad = true;
+        pos = end;
+    }
+    index[P] = bad ? in_bytes : pos;
+    if (bad) set_error(h, ICX_ECORRUPT);
 }
-cudaError_t launch_fastpfor_index(const uint8_t*, size_t, size_t, uint64_t*, WsHeader*, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// ------------------------------------------------------------ page parse
+
+constexpr int kMetaWarps = 4;
+constexpr int kWin = 4096;  // bytes of the byte array held in shared memory
+
+__global__ void __launch_bounds__(kMetaWarps * 32)
+    fastpfor_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n, const uint64_t* __restrict__ index,
+                         BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
+                         WsHeader* h) {
+    __shared__ __align__(16) uint32_t win_all[kMetaWarps][kWin / 4 + 4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
+    const size_t p = (size_t)blockIdx.x * kMetaWarps + warp;
+    if (p >= P) return;
+    uint32_t* win = win_all[warp];
+    const uint8_t* wb = reinterpret_cast<const uint8_t*>(win);
+    const uint32_t K = (uint32_t)min((size_t)kBlocksPerPage, nb - kBlocksPerPage * p);
+    BlockMeta* pm = meta + kBlocksPerPage * p;
+    uint32_t* pg = pmeta + kPageMetaWords * p;
+
+    const uint64_t base = index[p], end = index[p + 1];
+    bool bad = !(base <= end && end <= in_bytes && (base & 15) == 0 && end - base >= 16);
+    const uint8_t* page = in + base;
+    const size_t psize = bad ? 0 : end - base;
+    size_t len_at = 0, L = 0, bytes_at = 0;
+    if (!bad) {
+        len_at = 4 * (size_t)ld32(page);
+        bad = len_at < 16 || (len_at & 15) || len_at + 4 > psize;
+    }
+    if (!bad) {
+        L = ld32(page + len_at);
+        bytes_at = len_at + 4;
+        bad = bytes_at + pad_up(L, 4) + 4 > psize;
+    }
+    // sequential walk over the records (every lane follows it; lane k%32
+    // writes block k's record; lane d-1 keeps the running count of array d)
+    const size_t Lpad = pad_up(L, 4);
+    size_t win_start = 0, win_end = 0, r = 0, packed = 16;
+    uint32_t cnt = 0;
+    for (uint32_t k = 0; k < K && !bad; ++k) {
+        if (r + 131 > win_end && win_end < Lpad) {
+            __syncwarp();
+            win_start = r & ~(size_t)3;
+            const size_t words = min((size_t)(kWin / 4), (Lpad - win_start) / 4);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(page + bytes_at + win_start);
+            for (size_t i = lane; i < words; i += 32) win[i] = __ldg(src + i);
+            win_end = win_start + 4 * words;
+            __syncwarp();
+        }
+        if (r + 2 > L) {
+            bad = true;
+            break;
+        }
+        const size_t rb = r - win_start;
+        const uint32_t b = wb[rb], mb = wb[rb + 1];
+        if (b > 32 || mb > 32 || mb < b) {
+            bad = true;
+            break;
+        }
+        uint32_t c = 0, d = 0, cursor = 0, pos_off = 0, len = 2;
+        if (mb > b) {
+            c = wb[rb + 2];
+            if (c > 128) {  // a block holds 128 values
+                bad = true;
+                break;
+            }
+            d = mb - b;
+            len = 3 + c;
+            pos_off = (uint32_t)(bytes_at + r + 3);
+            cursor = __shfl_sync(FULL, cnt, d - 1);
+            if ((uint32_t)lane == d - 1) cnt += c;
+        }
+        if (r + len > L) {
+            bad = true;
+            break;
+        }
+        if ((uint32_t)lane == (k & 31)) {
+            BlockMeta m;
+            m.packed_off = (uint32_t)packed;
+            m.pos_off = pos_off;
+            m.cursor = cursor;
+            m.b = (uint8_t)b;
+            m.d = (uint8_t)d;
+            m.c = (uint8_t)c;
+            m.flags = 0;
+            pm[k] = m;
+        }
+        packed += 16 * b;
+        r += len;
+    }
+    if (!bad && packed != len_at) bad = true;
+    // exception arrays: offsets follow from the counts (lane d-1 checks the
+    // stored count of array d against the records)
+    uint32_t my_off = 0, my_cnt_at = 0;
+    if (!bad) {
+        const uint32_t bitset = ld32(page + bytes_at + Lpad);
+        size_t q = bytes_at + Lpad + 4;
+        for (int d = 1; d <= 32; ++d) {
+            const uint32_t nd = __shfl_sync(FULL, cnt, d - 1);
+            const bool has = (bitset >> (d - 1)) & 1u;
+            if (!has) {
+                if (nd) bad = true;
+                continue;
+            }
+            if (lane == d - 1) {
+                my_cnt_at = (uint32_t)q;
+                my_off = (uint32_t)pad_up(q + 4, 16);
+            }
+            q = pad_up(q + 4, 16) + 16 * (size_t)d * ((nd + 127) / 128);
+            if (q > psize) {
+                bad = true;
+                break;
+            }
+        }
+        if (pad_up(q, 16) != psize) bad = true;
+        // the stored count of every array must equal its records' total
+        if (!bad && ((bitset >> lane) & 1u) && ld32(page + my_cnt_at) != cnt) bad = true;
+        bad = __any_sync(FULL, bad);
+    }
+    pg[lane] = bad ? 0u : my_off;
+    if (lane == 0) pg[32] = bad ? 1u : 0u;
+    // per unit of 16 blocks: where its packed low bits start and how long they are
+    __syncwarp();
+    const uint32_t nunits = (K + 15) / 16;
+    if (!bad && (uint32_t)lane < nunits) {
+        const uint32_t k0 = 16 * lane, k1 = min(K, k0 + 16) - 1;
+        const uint32_t first = pm[k0].packed_off;
+        umeta[kUnitsPerPage * p + lane] = make_uint2(first, pm[k1].packed_off + 16 * pm[k1].b - first);
+    }
+    if (bad && lane == 0) set_error(h, ICX_ECORRUPT);
 }
-cudaError_t launch_fastpfor_encode(int, const uint32_t*, size_t, uint8_t*, size_t, uint64_t*, uint64_t*, void*,
-                                   size_t, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// ---------------------------------------------------------------- decode
+
+constexpr int kUnitMax = 16 * 16 * 32;  // packed bytes of 16 blocks at width 32
+constexpr int kFBuf = kUnitMax + 128;
+
+struct FpSmem {
+    uint64_t bar[kWarps];
+    BlockMeta m[kWarps][16];
+    uint8_t blk_of[kWarps][16 * 128];  // block of the unit's q-th exception
+};
+
+// Each warp is an independent pipeline over units of 16 blocks (the same
+// structure as the SIMD-BP128 decoder); the next unit's block records and
+// page offsets are loaded while the current unit's copy is in flight.
+template <int DELTA>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+    fastpfor_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
+                           const uint64_t* __restrict__ index, const BlockMeta* __restrict__ meta,
+                           const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, WsHeader* h) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    FpSmem& S = *reinterpret_cast<FpSmem*>(smem_raw);
+    uint8_t* bufs = smem_raw + ((sizeof(FpSmem) + 127) / 128) * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t* buf = bufs + (size_t)warp * kFBuf;
+    uint32_t* buf32 = reinterpret_cast<uint32_t*>(buf);
+    uint64_t* bar = &S.bar[warp];
+    BlockMeta* m = S.m[warp];
+    uint8_t* blk_of = S.blk_of[warp];
+    const size_t nb = n / 128;
+    const uint32_t U = (uint32_t)((nb + 15) / 16);  // units of 16 blocks
+    const uint32_t P = (uint32_t)((nb + kBlocksPerPage - 1) / kBlocksPerPage);
+    const uint32_t units = U + 1;                   // then the Variable Byte tail
+    const uint32_t epoch = launch_epoch(h);
+    if (lane == 0) mbar_init(bar, 1);
+    fence_mbar_init();
+    __syncwarp();
+    uint32_t phase = 0;
+
+    // next unit's records: lane 0 its page base, page flag and packed region,
+    // lanes 0..15 its block records
+    uint64_t pbase_n = 0;
+    uint2 um_n = make_uint2(0, 0);
+    uint32_t bad_n = 0;
+    uint4 mrec_n = make_uint4(0, 0, 0, 0);
+    auto prefetch = [&](uint32_t uu) {
+        if (uu < U) {
+            const uint32_t p = uu / kUnitsPerPage;
+            const uint32_t K = (uint32_t)min((size_t)16, nb - 16 * (size_t)uu);
+            if (lane == 0) {
+                pbase_n = index[p];
+                um_n = umeta[uu];
+                bad_n = pmeta[kPageMetaWords * p + 32];
+            }
+            if ((uint32_t)lane < K) mrec_n = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
+        }
+    };
+    // publishes the prefetched records and starts the unit's bulk copy;
+    // returns 0 = nothing to wait for, 1 = copy in flight, 2 = bad page
+    auto issue = [&](uint32_t uu) -> uint32_t {
+        uint32_t r = 0;
+        if (uu < U) {
+            if (lane < 16) reinterpret_cast<uint4*>(m)[lane] = mrec_n;
+            __syncwarp();
+            if (lane == 0) {
+                if (bad_n) {
+                    r = 2;
+                } else if (um_n.y) {
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, um_n.y);
+                    bulk_load(buf, in + pbase_n + um_n.x, um_n.y, bar);
+                    r = 1;
+                }
+            }
+        }
+        return __shfl_sync(FULL, r, 0);
+    };
+
+    uint32_t u = warp_grab(h);
+    prefetch(u);
+    uint64_t pbase = __shfl_sync(FULL, pbase_n, 0);
+    uint32_t st = issue(u);
+    uint32_t grabbed = 0;
+    if (lane == 0) grabbed = atomicAdd(&h->tile_counter, 1u);
+    while (u < units) {
+        const uint32_t un = __shfl_sync(FULL, grabbed, 0);
+        prefetch(un);
+        if (lane == 0) grabbed = atomicAdd(&h->tile_counter, 1u);
+        uint4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
+        uint32_t K = 0;
+        if (u < U) {
+            K = (uint32_t)min((size_t)16, nb - 16 * (size_t)u);
+            const uint32_t* pg = pmeta + kPageMetaWords * (u / kUnitsPerPage);
+            bool ok = st != 2;
+            if (!ok) {
+                if (lane == 0) set_error(h, ICX_ECORRUPT);
+            } else if (st == 1) {
+                ok = __all_sync(FULL, mbar_wait(bar, phase));
+                phase ^= 1;
+                if (!ok && lane == 0) set_error(h, ICX_ETIMEOUT);
+            }
+            if (ok) {
+                const uint32_t first = m[0].packed_off;
+                uint32_t C = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if ((uint32_t)k < K) {
+                        const uint32_t b = m[k].b;
+                        const uint32_t bit = (uint32_t)lane * b;
+                        const uint4* rows = reinterpret_cast<const uint4*>(buf + (m[k].packed_off - first));
+                        const uint4 r0 = rows[bit >> 5], r1 = rows[(bit >> 5) + 1];
+                        const uint32_t s = bit & 31, mask = width_mask(b);
+                        v[k] = make_uint4(__funnelshift_r(r0.x, r1.x, s) & mask, __funnelshift_r(r0.y, r1.y, s) & mask,
+                                          __funnelshift_r(r0.z, r1.z, s) & mask,
+                                          __funnelshift_r(r0.w, r1.w, s) & mask);
+                        C += m[k].c;
+                    }
+                }
+                if (C) {
+                    // patch: high << b of every exception of the unit (Sec. 5)
+                    __syncwarp();
+                    uint32_t pre[16];
+                    uint32_t run = 0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        pre[k] = run;
+                        const uint32_t c = (uint32_t)k < K ? m[k].c : 0u;
+                        for (uint32_t j = lane; j < c; j += 32) blk_of[run + j] = (uint8_t)k;
+                        if (c) reinterpret_cast<uint4*>(buf + 512 * k)[lane] = make_uint4(0, 0, 0, 0);
+                        run += c;
+                    }
+                    __syncwarp();
+                    bool badpos = false;
+                    // four independent exceptions per lane per round, so their
+                    // loads are in flight together
+                    for (uint32_t q0 = 0; q0 < C; q0 += 128) {
+                        uint32_t kk[4], pos[4], lo[4], hi[4], sh[4], dw[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint32_t q = q0 + 32 * i + lane;
+                            kk[i] = 0xFFu;
+                            if (q < C) {
+                                const uint32_t k = blk_of[q];
+                                const BlockMeta mk = m[k];
+                                uint32_t pk = 0;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if ((uint32_t)j == k) pk = pre[j];
+                                const uint32_t jj = q - pk;
+                                const uint32_t d = mk.d, e = mk.cursor + jj;
+                                const uint8_t* arr = in + pbase + pg[d - 1] + 16 * (size_t)d * (e >> 7);
+                                const uint32_t ii = e & 127, bit = (ii >> 2) * d;
+                                const uint8_t* wp = arr + 16 * (bit >> 5) + 4 * (ii & 3);
+                                kk[i] = k;
+                                sh[i] = bit & 31;
+                                dw[i] = d;
+                                pos[i] = in[pbase + mk.pos_off + jj];
+                                lo[i] = ld32(wp);
+                                hi[i] = (bit & 31) + d > 32 ? ld32(wp + 16) : 0u;
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (kk[i] != 0xFFu) {
+                                const uint32_t high = __funnelshift_r(lo[i], hi[i], sh[i]) & width_mask(dw[i]);
+                                if (pos[i] < 128)
+                                    atomicOr(&buf32[128 * kk[i] + pos[i]], high << m[kk[i]].b);
+                                else
+                                    badpos = true;
+                            }
+                        }
+                    }
+                    if (__any_sync(FULL, badpos) && lane == 0) set_error(h, ICX_ECORRUPT);
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        if ((uint32_t)k < K && m[k].c) {
+                            const uint4 pv = reinterpret_cast<const uint4*>(buf + 512 * k)[lane];
+                            v[k].x |= pv.x;
+                            v[k].y |= pv.y;
+                            v[k].z |= pv.z;
+                            v[k].w |= pv.w;
+                        }
+                    }
+                }
+            }
+        } else if (u == U) {
+            const uint32_t count = (uint32_t)(n - 128 * nb);
+            if (count) {
+                tail_unit(in, in_bytes, index[P], count, buf32, v, h, lane);
+                K = 1;
+            }
+        }
+        __syncwarp();  // buffer and records of unit u are no longer read
+        const uint64_t pbase_next = __shfl_sync(FULL, pbase_n, 0);
+        const uint32_t st_n = issue(un);
+        const uint4 agg = unit_local_scan<DELTA>(v, K, false, lane);
+        const uint4 pref = warp_unit_prefix<DELTA>(agg, u, epoch, h);
+        store_unit(out, u < U ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
+        u = un;
+        st = st_n;
+        pbase = pbase_next;
+    }
+    finish_launch(h, epoch);
+}
+
+// ------------------------------------------------------------ launchers
+
+cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, uint64_t* index, WsHeader* h,
+                                  cudaStream_t s) {
+    fastpfor_index_kernel<<<1, 32, 0, s>>>(in, in_bytes, n, index, h);
+    return cudaGetLastError();
+}
+
+template <int DELTA>
+static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
+                             WsHeader* h, cudaStream_t s) {
+    auto kern = fastpfor_decode_kernel<DELTA>;
+    const int smem = (int)(((sizeof(FpSmem) + 127) / 128) * 128 + (size_t)kWarps * kFBuf);
+    static int blocks_per_sm = -1;
+    static int sms = 0;
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kWarps * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    char* ws = reinterpret_cast<char*>(h);
+    BlockMeta* meta = reinterpret_cast<BlockMeta*>(ws + ws_blockmeta_off(n));
+    uint32_t* pmeta = reinterpret_cast<uint32_t*>(ws + ws_pagemeta_off(n));
+    uint2* umeta = reinterpret_cast<uint2*>(ws + ws_unitmeta_off(n));
+    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, U = (nb + 15) / 16;
+    if (P > 0) {
+        fastpfor_meta_kernel<<<(unsigned)((P + kMetaWarps - 1) / kMetaWarps), kMetaWarps * 32, 0, s>>>(
+            in, in_bytes, n, index, meta, pmeta, umeta, h);
+    }
+    const size_t ntiles = (U + 1 + kWarps - 1) / kWarps;
+    const int grid = (int)min((size_t)blocks_per_sm * sms, ntiles);
+    kern<<<grid, kWarps * 32, smem, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fastpfor_decode(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                   const uint64_t* index, WsHeader* h, cudaStream_t s) {
+    if (delta == ICX_DELTA_1) return launch_fp<ICX_DELTA_1>(in, in_bytes, out, n, index, h, s);
+    if (delta == ICX_DELTA_4) return launch_fp<ICX_DELTA_4>(in, in_bytes, out, n, index, h, s);
+    return launch_fp<ICX_DELTA_NONE>(in, in_bytes, out, n, index, h, s);
 }
 
 }  // namespace icx

@@ -23,4 +23,6 @@ cudaError_t launch_fastpfor_encode(int delta, const uint32_t* x, size_t n, uint8
                                    uint64_t* index, uint64_t* out_bytes, void* ws, size_t ws_bytes,
                                    cudaStream_t s);
 
+size_t fastpfor_encode_workspace_bytes(size_t n);
+
 }  // namespace icx

@@ -1,0 +1,192 @@
+// The tile epilogue shared by the decoders: a CTA of kWarps warps decodes
+// kWarps consecutive units of up to 16 blocks (2048 integers, 64 per lane in
+// registers), then
+//   1. each warp scans its unit locally (differential decoding, Sec. 3),
+//   2. warp 0 scans the kWarps unit aggregates and runs one decoupled
+//      look-back for the whole tile to get the carry-in,
+//   3. every warp adds its prefix and stores with 128-bit stores.
+#pragma once
+
+#include "icx_device.cuh"
+
+namespace icx {
+
+constexpr int kWarps = 8;
+
+struct TileShared {
+    uint4 agg[kWarps];
+    uint4 pref[kWarps];
+    uint32_t tile;
+    uint32_t pad[3];
+};
+
+// Local scan of a unit held in row ownership (lane t: integers 128k + 4t..+3
+// of block k in v[k]); `residue` means the values arrive in W32 residue
+// ownership and are moved to row ownership here.  Returns the unit aggregate
+// (stride 1: .x; stride 4: one per residue).
+template <int DELTA>
+__device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, bool residue, int lane) {
+    uint4 agg = make_uint4(0, 0, 0, 0);
+    if (DELTA == ICX_DELTA_4 && residue) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((uint32_t)k < K) v[k] = residue_to_row(residue_scan_d4(v[k], carry, lane), lane);
+        agg.x = __shfl_sync(FULL, carry, 0);
+        agg.y = __shfl_sync(FULL, carry, 1);
+        agg.z = __shfl_sync(FULL, carry, 2);
+        agg.w = __shfl_sync(FULL, carry, 3);
+        return agg;
+    }
+    if (residue) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((uint32_t)k < K) v[k] = residue_to_row(v[k], lane);
+    }
+    if (DELTA == ICX_DELTA_1) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((uint32_t)k < K) v[k] = row_scan_d1(v[k], carry, lane);
+        agg.x = carry;
+    } else if (DELTA == ICX_DELTA_4) {
+        uint4 carry = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((uint32_t)k < K) v[k] = row_scan_d4(v[k], carry, lane);
+        agg = carry;
+    }
+    return agg;
+}
+
+// CTA-wide: exclusive prefix of this warp's unit (tile carry-in from the
+// look-back plus the aggregates of the tile's earlier units).  Contains two
+// __syncthreads; every thread of the CTA must call it.
+template <int DELTA>
+__device__ __forceinline__ uint4 tile_prefix(TileShared& S, uint4 agg, uint32_t tile, uint32_t epoch, WsHeader* h,
+                                             int warp, int lane) {
+    if (DELTA == ICX_DELTA_NONE) return make_uint4(0, 0, 0, 0);
+    if (lane == 0) S.agg[warp] = agg;
+    __syncthreads();
+    if (warp == 0) {
+        const uint4 mine = lane < kWarps ? S.agg[lane] : make_uint4(0, 0, 0, 0);
+        uint4 incl = mine;
+#pragma unroll
+        for (int off = 1; off < kWarps; off <<= 1) {
+            uint4 y = make_uint4(__shfl_up_sync(FULL, incl.x, off), __shfl_up_sync(FULL, incl.y, off),
+                                 __shfl_up_sync(FULL, incl.z, off), __shfl_up_sync(FULL, incl.w, off));
+            if (lane >= off) incl = add4(incl, y);
+        }
+        const uint4 total = shfl4(incl, kWarps - 1);
+        const uint4 base = DELTA == ICX_DELTA_1 ? lookback<1>(h, epoch, tile, total)
+                                                : lookback<4>(h, epoch, tile, total);
+        if (lane < kWarps) S.pref[lane] = add4(base, sub4(incl, mine));
+    }
+    __syncthreads();
+    uint4 pref = S.pref[warp];
+    if (DELTA == ICX_DELTA_1) pref = make_uint4(pref.x, pref.x, pref.x, pref.x);
+    return pref;
+}
+
+// Stores blocks 0..K-1 of a unit whose first integer is `first`; integers at
+// or beyond n are dropped (the Variable Byte tail unit).
+__device__ __forceinline__ void store_unit(uint32_t* __restrict__ out, size_t first, size_t n, const uint4 (&v)[16],
+                                           uint32_t K, uint4 pref, int lane) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if ((uint32_t)k < K) {
+            const size_t p = first + 128 * (size_t)k + 4 * (size_t)lane;
+            const uint4 r = add4(v[k], pref);
+            if (p + 4 <= n) {
+                *reinterpret_cast<uint4*>(out + p) = r;
+            } else {
+                for (int c = 0; c < 4; ++c)
+                    if (p + c < n) out[p + c] = comp(r, c);
+            }
+        }
+    }
+}
+
+// Exclusive prefix of a unit decoded by one warp on its own: one decoupled
+// look-back per unit (no CTA barrier), stride-1 carries splatted to 4 lanes.
+template <int DELTA>
+__device__ __forceinline__ uint4 warp_unit_prefix(uint4 agg, uint32_t unit, uint32_t epoch, WsHeader* h) {
+    if (DELTA == ICX_DELTA_NONE) return make_uint4(0, 0, 0, 0);
+    if (DELTA == ICX_DELTA_1) {
+        const uint4 b = lookback<1>(h, epoch, unit, agg);
+        return make_uint4(b.x, b.x, b.x, b.x);
+    }
+    return lookback<4>(h, epoch, unit, agg);
+}
+
+// Next unit id for a warp (lane 0 takes it from the launch's counter).
+__device__ __forceinline__ uint32_t warp_grab(WsHeader* h) {
+    uint32_t u = 0;
+    if ((threadIdx.x & 31) == 0) u = atomicAdd(&h->tile_counter, 1u);
+    return __shfl_sync(FULL, u, 0);
+}
+
+// Grabs the next tile id for the CTA (thread 0), broadcast through S.tile.
+__device__ __forceinline__ uint32_t next_tile(TileShared& S, WsHeader* h) {
+    if (threadIdx.x == 0) S.tile = atomicAdd(&h->tile_counter, 1u);
+    __syncthreads();
+    return S.tile;
+}
+
+// ----------------------------------------------------------- tail (VByte)
+
+// Warp-parallel Variable Byte decoder (Sec. 2.4): 32 bytes per step; a
+// ballot of the terminating bytes gives every byte its integer and its group
+// position.  Decodes `count` (<= 127) integers starting at in[start] into
+// vals[0..127] (zero-filled).  Returns false (and records ECORRUPT) on a
+// truncated stream or an integer above 32 bits / 5 bytes.
+__device__ __forceinline__ bool vbyte_decode_warp(const uint8_t* __restrict__ in, size_t start, size_t in_bytes,
+                                  uint32_t count, uint32_t* vals, WsHeader* h) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < 128; i += 32) vals[i] = 0;
+    __syncwarp();
+    uint32_t k0 = 0, carry = 0;
+    size_t pos = start;
+    bool bad = false;
+    while (k0 < count) {
+        const size_t p = pos + lane;
+        const bool have = p < in_bytes;
+        const uint32_t byte = have ? in[p] : 0u;
+        const unsigned have_mask = __ballot_sync(FULL, have);
+        const unsigned term = __ballot_sync(FULL, have && (byte & 0x80u));
+        const unsigned before = term & ((1u << lane) - 1u);
+        const uint32_t idx = k0 + __popc(before);
+        const uint32_t posin = before ? (uint32_t)(lane - (31 - __clz(before)) - 1) : carry + lane;
+        if (have && idx < count) {
+            if (posin > 4 || (posin == 4 && (byte & 0x70u)))
+                bad = true;
+            else
+                atomicOr(&vals[idx], (byte & 0x7Fu) << (7 * posin));
+        }
+        k0 += __popc(term);
+        carry = term ? (uint32_t)(__clz(term)) : carry + 32;
+        pos += 32;
+        if (have_mask != FULL) {
+            if (k0 < count) bad = true;
+            break;
+        }
+    }
+    bad = __any_sync(FULL, bad);
+    if (bad && lane == 0) set_error(h, ICX_ECORRUPT);
+    __syncwarp();
+    return !bad;
+}
+
+
+// Decodes the Variable Byte tail (count <= 127 integers at in[start]) into
+// row ownership of block 0 (scratch: 128 words of shared memory).
+__device__ __forceinline__ void tail_unit(const uint8_t* __restrict__ in, size_t in_bytes, uint64_t start,
+                                          uint32_t count, uint32_t* scratch, uint4 (&v)[16], WsHeader* h, int lane) {
+    if (start <= in_bytes && vbyte_decode_warp(in, start, in_bytes, count, scratch, h))
+        v[0] = *reinterpret_cast<const uint4*>(scratch + 4 * lane);
+    else if (start > in_bytes && lane == 0)
+        set_error(h, ICX_ECORRUPT);
+    __syncwarp();
+}
+
+}  // namespace icx
