@@ -146,6 +146,32 @@ icx_status fastpfor_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out
 icx_status delta_decode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_delta delta,
                         void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
 
+/* Allocation-free variant of bp128_decode for callers that cannot allocate
+ * device memory -- code that must not call cudaMalloc (an allocation-free
+ * runtime, a host application that owns every device allocation, a plugin
+ * whose host forbids allocations on its hot path).  The paper has no
+ * counterpart: it is a calling convention of this library, not a step of
+ * the method.
+ *
+ * Instead of a caller-provided workspace it uses one file-scope device array
+ * of about 4 MiB inside the library, enough for n <= 2^28 integers; a larger
+ * n returns ICX_ENOSPC without launching anything.  Every GPU that loads the
+ * library holds that array until the process exits.  The caller still passes
+ * the stream, its index (NULL allowed for a single metablock, as in
+ * bp128_decode), the output and, optionally, d_status: a device word that
+ * receives the call's data-dependent status (icx_status) once the stream
+ * reaches it.  No allocation happens in this call, and it calls no
+ * allocating library routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: two calls that
+ * overlap on the GPU (other streams, other host threads) race and give wrong
+ * results; serialise them. */
+icx_status bp128_decode_static(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, size_t n,
+                               icx_delta delta, icx_layout fmt, const uint64_t *d_index,
+                               uint32_t *d_status, icx_stream_t stream);
+
 /* ------------------------------------------------------------ encode ---- */
 
 /* Differential coding (Sec. 3): d_out[i] = d_in[i] - d_in[i-s].  d_out must
