@@ -205,6 +205,8 @@ def run_gpu(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     icx.lib()  # fails loudly if the CUDA library is missing
+    if args.bp128_warps:
+        icx.set_tuning("bp128.warps_per_cta", args.bp128_warps)
     arrays = workload_arrays(args.n)
     stream = torch.cuda.current_stream()
 
@@ -212,7 +214,9 @@ def run_gpu(args, world, rank, local):
     streams = []
     for name, x in arrays.items():
         xt = torch.from_numpy(x).to(dev)
-        for codec, delta, fmt, label in COMBOS:
+        combos = COMBOS + ([("bp128", 0, 0, "SIMD-BP128 (no delta)"), ("bp128", 0, 1, "W32 (no delta)")]
+                           if args.extra_none else [])
+        for codec, delta, fmt, label in combos:
             if codec == "fastpfor" and args.skip_fastpfor:
                 continue
             enc = icx.bp128_encode(xt, delta, fmt) if codec == "bp128" else icx.fastpfor_encode(xt, delta)
@@ -330,7 +334,8 @@ def workload_label(arrays, streams):
     for name, x in arrays.items():
         parts.append(f"{name} n={x.size}" + (" (2^26 in [0,2^29))" if name == "uniform" and x.size == 1 << 26
                                                else " (1024 clusters, 2^18 windows)" if name == "clustered" else ""))
-    labels = sorted({s["label"] for s in streams}, key=lambda l: [c[3] for c in COMBOS].index(l))
+    order = [c[3] for c in COMBOS]
+    labels = sorted({s["label"] for s in streams}, key=lambda l: order.index(l) if l in order else len(order))
     return (f"long sorted uint32 arrays, {len(streams)} decodes per step: {{" + "; ".join(parts) + "} x {"
             + ", ".join(labels) + "}")
 
@@ -455,7 +460,9 @@ def main():
     ap.add_argument("--cpu-prefix", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fastpfor", action="store_true")
+    ap.add_argument("--extra-none", action="store_true", help="also time decodes without differential decoding")
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
+    ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

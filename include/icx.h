@@ -196,6 +196,12 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, uint8
                            void *d_encode_workspace, size_t encode_workspace_bytes,
                            icx_stream_t stream);
 
+/* Sets a launch parameter of the decoders (not part of the method):
+ * "bp128.warps_per_cta" = 4, 8 or 16 warps per CTA tile of the SIMD-BP128 /
+ * W32 decoder (0 = default: 4 for stride-4 deltas, 8 otherwise).  Takes effect for later launches; not thread
+ * safe against concurrent launches.  ICX_EINVAL for an unknown key. */
+icx_status icx_set_tuning(const char *key, int value);
+
 /* Library version string. */
 const char *icx_version(void);
 

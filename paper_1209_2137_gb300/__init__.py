@@ -70,6 +70,7 @@ def lib():
                 "bp128_encode": ([vp, sz, i, i, vp, sz, vp, vp, vp, sz, vp], i),
                 "fastpfor_encode": ([vp, sz, i, vp, sz, vp, vp, vp, sz, vp], i),
                 "icx_version": ([], ctypes.c_char_p),
+                "icx_set_tuning": ([ctypes.c_char_p, i], i),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -81,7 +82,7 @@ def lib():
 EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_bytes", "icx_fastpfor_max_bytes",
             "icx_workspace_bytes", "icx_encode_workspace_bytes", "icx_workspace_init", "icx_status_read",
             "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "delta_decode", "delta_encode",
-            "bp128_encode", "fastpfor_encode", "icx_version")
+            "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning")
 
 
 def _check(code: int, what: str):
@@ -304,6 +305,11 @@ def decode(enc: Encoded, out=None, workspace=None, stream=None):
     if enc.codec == "bp128":
         return bp128_decode(enc.data, enc.n, enc.delta, enc.fmt, enc.index, out, workspace, stream)
     return fastpfor_decode(enc.data, enc.n, enc.delta, enc.index, out, workspace, stream)
+
+
+def set_tuning(key: str, value: int) -> None:
+    """Launch parameter of the decoders, e.g. ("bp128.warps_per_cta", 4)."""
+    _check(lib().icx_set_tuning(key.encode(), int(value)), f"icx_set_tuning({key})")
 
 
 def version() -> str:

@@ -181,4 +181,13 @@ icx_status fastpfor_encode(const uint32_t* d_x, size_t n, icx_delta delta, uint8
 
 const char* icx_version(void) { return "icx 0.1 (sm_103a)"; }
 
+icx_status icx_set_tuning(const char* key, int value) {
+    if (!key) return ICX_EINVAL;
+    if (!strcmp(key, "bp128.warps_per_cta")) {
+        icx::set_bp128_warps(value);
+        return ICX_OK;
+    }
+    return ICX_EINVAL;
+}
+
 }  // extern "C"

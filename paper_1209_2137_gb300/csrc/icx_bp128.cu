@@ -2,7 +2,7 @@
 // Sec. 2.4 Variable Byte tail) fused with differential decoding (Sec. 3), the
 // sequential index walk, and the standalone differential decoder.
 //
-// One CTA of 8 warps takes a tile of 8 consecutive units; unit u < M is
+// A CTA of W warps takes a tile of W consecutive units; unit u < M is
 // metablock u (2048 integers), unit M is the Variable Byte tail.  A warp
 // stages its metablock into shared memory with one bulk copy, unpacks the 16
 // blocks into registers (64 integers per lane), scans them locally, and the
@@ -16,6 +16,8 @@ namespace icx {
 // ---------------------------------------------------------------- decode
 
 constexpr int kMetaMax = 16 + 16 * 16 * 32;  // 8208: every width 32
+constexpr int kPipeHdr = 1024;                // TileShared, then two mbarriers per warp
+static_assert(sizeof(TileShared) + 16 * kMaxWarps <= kPipeHdr, "tile header");
 constexpr int kBuf = kMetaMax + 128;         // slack for reading one row past
 
 
@@ -46,63 +48,35 @@ __device__ __forceinline__ uint4 unpack_block(const uint8_t* buf, uint32_t base_
     }
 }
 
-// Each warp is an independent pipeline over units (metablocks, then the tail):
-// wait for unit u's bulk copy, unpack it into registers, start the copy of
-// the next unit into the freed buffer, then scan, look back and store unit u.
-template <int DELTA, int FMT>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+// A CTA of W warps takes tiles of W consecutive units (unit u < M is
+// metablock u, unit M the Variable Byte tail); tile ids come from the
+// launch's counter when the CTA starts on them, so every tile that exists is
+// being worked on (the look-back never waits on an idle tile).  Per warp:
+// one bulk copy of its metablock into its shared buffer, unpack into
+// registers (64 integers per lane), local scan; then one look-back per tile
+// and 128-bit stores.
+template <int DELTA, int FMT, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
     bp128_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out,
                         size_t n, const uint64_t* __restrict__ index, WsHeader* h) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
+    TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw) + warp;
-    uint8_t* buf = smem_raw + 128 + (size_t)warp * kBuf;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kPipeHdr) - 2 * kMaxWarps + 2 * warp;
+    uint8_t* buf = smem_raw + kPipeHdr + (size_t)warp * kBuf;
     const size_t nb = n / 128;
     const uint32_t M = (uint32_t)((nb + 15) / 16);
-    const uint32_t units = M + 1;  // metablocks, then the Variable Byte tail
+    const uint32_t ntiles = (M + 1 + W - 1) / W;
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
-    __syncwarp();
+    __syncthreads();
     uint32_t phase = 0;
 
-    // Unit ids come from the launch's counter one step ahead (the atomic's
-    // result is used one iteration later), and the index entries of the next
-    // unit are loaded while the current unit's copy is in flight.
-    uint32_t u = warp_grab(h);
-    uint64_t off_n = 0, end_n = 0;
-    if (lane == 0 && u < M) {
-        off_n = index[u];
-        end_n = index[u + 1];
-    }
-    // Starts the bulk copy of metablock u (lane 0 holds its index entries);
-    // returns its size, 0 if there is nothing to copy, ~0u if the entries are bad.
-    auto issue = [&](uint32_t uu, uint64_t off, uint64_t end) -> uint32_t {
-        uint32_t r = 0;
-        if (lane == 0 && uu < M) {
-            const bool ok = off <= end && end <= in_bytes && end - off >= 16 && end - off <= kMetaMax &&
-                            ((off | end) & 15) == 0;
-            r = ok ? (uint32_t)(end - off) : ~0u;
-            if (ok) {
-                fence_proxy_async();
-                mbar_expect_tx(bar, r);
-                bulk_load(buf, in + off, r, bar);
-            }
-        }
-        return __shfl_sync(FULL, r, 0);
-    };
-    uint32_t size = issue(u, off_n, end_n);
-    uint32_t grabbed = 0;
-    if (lane == 0) grabbed = atomicAdd(&h->tile_counter, 1u);
-    while (u < units) {
-        const uint32_t un = __shfl_sync(FULL, grabbed, 0);
-        if (lane == 0) {
-            if (un < M) {
-                off_n = index[un];
-                end_n = index[un + 1];
-            }
-            grabbed = atomicAdd(&h->tile_counter, 1u);
-        }
+    for (;;) {
+        const uint32_t tile = next_tile(S, h);
+        if (tile >= ntiles) break;
+        const uint32_t u = tile * W + warp;
         uint4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
@@ -110,6 +84,19 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         bool residue = false;  // W32 metablocks arrive in residue ownership
         if (u < M) {
             K = (uint32_t)min((size_t)16, nb - 16 * (size_t)u);
+            uint32_t size = 0;
+            if (lane == 0) {
+                const uint64_t off = index[u], end = index[u + 1];
+                const bool ok = off <= end && end <= in_bytes && end - off >= 16 && end - off <= kMetaMax &&
+                                ((off | end) & 15) == 0;
+                size = ok ? (uint32_t)(end - off) : ~0u;
+                if (ok) {
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, size);
+                    bulk_load(buf, in + off, size, bar);
+                }
+            }
+            size = __shfl_sync(FULL, size, 0);
             bool ok = size != ~0u;
             if (!ok) {
                 if (lane == 0) set_error(h, ICX_ECORRUPT);
@@ -146,6 +133,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                     residue = FMT == ICX_FMT_W32;
                 }
             }
+            __syncwarp();
         } else if (u == M) {
             // Variable Byte tail: n % 128 integers after the last metablock,
             // decoded into row ownership of one block.
@@ -155,13 +143,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 K = 1;
             }
         }
-        __syncwarp();  // every lane is done with the buffer
-        const uint32_t size_n = issue(un, off_n, end_n);
-        const uint4 agg = unit_local_scan<DELTA>(v, K, residue, lane);
-        const uint4 pref = warp_unit_prefix<DELTA>(agg, u, epoch, h);
-        store_unit(out, u < M ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
-        u = un;
-        size = size_n;
+        uint4 agg;
+        if (DELTA == ICX_DELTA_4 && FMT == ICX_FMT_PAPER)
+            agg = unit_scan_d4_smem(v, reinterpret_cast<uint32_t*>(buf), lane);
+        else
+            agg = unit_local_scan<DELTA>(v, K, residue, lane);
+        const uint4 pref = tile_prefix<DELTA, W>(S, agg, tile, epoch, h, warp, lane);
+        if (u <= M) store_unit(out, u < M ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
+        if (DELTA == ICX_DELTA_NONE) __syncthreads();  // S.tile is rewritten next iteration
     }
     finish_launch(h, epoch);
 }
@@ -203,14 +192,20 @@ __global__ void bp128_index_kernel(const uint8_t* __restrict__ in, size_t in_byt
 // Tile = 8 warps x 2048 integers; lanes load row-owned uint4s (coalesced),
 // scan, look back, store.  In place is safe: every element is read and
 // written by the same lane.
+// CTA tiles of kWarps x 2048 integers: coalesced 128-bit loads in row
+// ownership, local scan, one look-back per tile, stores.  In place is safe:
+// every element is read and written by the same lane.
 template <int DELTA>
 __global__ void __launch_bounds__(kWarps * 32, 2)
     delta_decode_kernel(const uint32_t* in, uint32_t* out, size_t n, WsHeader* h) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t units = (uint32_t)((n + 2047) / 2048);
+    __shared__ TileShared S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ntiles = (uint32_t)((n + 2048 * kWarps - 1) / (2048 * kWarps));
     const uint32_t epoch = launch_epoch(h);
-    for (uint32_t u = warp_grab(h); u < units; u = warp_grab(h)) {
-        const size_t base = (size_t)u * 2048;
+    for (;;) {
+        const uint32_t tile = next_tile(S, h);
+        if (tile >= ntiles) break;
+        const size_t base = ((size_t)tile * kWarps + warp) * 2048;
         uint4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -223,19 +218,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             }
         }
         const uint4 agg = unit_local_scan<DELTA>(v, 16, false, lane);
-        const uint4 pref = warp_unit_prefix<DELTA>(agg, u, epoch, h);
+        const uint4 pref = tile_prefix<DELTA>(S, agg, tile, epoch, h, warp, lane);
         store_unit(out, base, n, v, 16, pref, lane);
+        __syncthreads();
     }
     finish_launch(h, epoch);
 }
 
 // ------------------------------------------------------------ launchers
 
-template <int DELTA, int FMT>
+template <int DELTA, int FMT, int W>
 static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                 const uint64_t* index, WsHeader* h, cudaStream_t s) {
-    auto kern = bp128_decode_kernel<DELTA, FMT>;
-    const int smem = (int)(128 + (size_t)kWarps * kBuf);
+    auto kern = bp128_decode_kernel<DELTA, FMT, W>;
+    const int smem = (int)(kPipeHdr + (size_t)W * kBuf);
     static int blocks_per_sm = -1;
     static int sms = 0;
     if (blocks_per_sm < 0) {
@@ -244,21 +240,43 @@ static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* ou
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kWarps * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, W * 32, smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     const size_t M = (n / 128 + 15) / 16;
-    const size_t ctas = (M + 1 + kWarps - 1) / kWarps;
+    const size_t ctas = (M + 1 + W - 1) / W;
     const int grid = (int)min((size_t)blocks_per_sm * sms, ctas);
-    kern<<<grid, kWarps * 32, smem, s>>>(in, in_bytes, out, n, index, h);
+    kern<<<grid, W * 32, smem, s>>>(in, in_bytes, out, n, index, h);
     return cudaGetLastError();
+}
+
+
+
+
+
+
+
+
+static int g_bp128_warps = 0;  // warps per CTA of the SIMD-BP128 decoder (0 = per-stride default)
+
+void set_bp128_warps(int w) { g_bp128_warps = (w == 4 || w == 8 || w == 16) ? w : 0; }
+
+template <int DELTA, int FMT>
+static cudaError_t launch_bp128_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                  const uint64_t* index, WsHeader* h, cudaStream_t s) {
+    // measured on the 2^26 sorted workload: 4 warps per CTA suit the stride-4
+    // scan (more CTAs per SM), 8 the others
+    const int w = g_bp128_warps ? g_bp128_warps : (DELTA == ICX_DELTA_4 ? 4 : 8);
+    if (w == 4) return launch_bp128<DELTA, FMT, 4>(in, in_bytes, out, n, index, h, s);
+    if (w == 16) return launch_bp128<DELTA, FMT, 16>(in, in_bytes, out, n, index, h, s);
+    return launch_bp128<DELTA, FMT, 8>(in, in_bytes, out, n, index, h, s);
 }
 
 cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
                                 size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s) {
 #define ICX_CASE(D, F) \
-    if (delta == D && fmt == F) return launch_bp128<D, F>(in, in_bytes, out, n, index, h, s);
+    if (delta == D && fmt == F) return launch_bp128_w<D, F>(in, in_bytes, out, n, index, h, s);
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_PAPER)
     ICX_CASE(ICX_DELTA_1, ICX_FMT_PAPER)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_PAPER)

@@ -264,67 +264,105 @@ __device__ __forceinline__ uint4 residue_to_row(uint4 a, int lane) {
 
 // ------------------------------------------------------------- look-back
 
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b) {
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
 // Decoupled look-back for tile `tile`, run by one full warp.  NL is the
 // number of independent chains (1 for stride 1, 4 for stride 4); agg holds
-// the tile's NL aggregates.  Returns the exclusive prefixes (components
-// 0..NL-1) and publishes the inclusive ones.  Every wait is bounded: after
-// kWaitLimitNs without progress the status word gets ICX_ETIMEOUT and the
-// tile publishes what it has, so no other tile can wait forever on it.
-template <int NL>
+// the tile's NL aggregates.  A tile's state is NL 64-bit words, each (epoch
+// tag | flag | 32-bit value), written by NL relaxed stores; a reader counts a
+// state only if all its NL tags agree (mixed tags mean the owner is between
+// its two publications and are waited out).  Every round trip inspects 32*R
+// predecessors: lane i reads the state of tile end-1-i-32r with one or two
+// 128-bit loads.  Contributions are summed per lane and reduced once at the
+// end.  Returns the exclusive prefixes (components 0..NL-1) and publishes the
+// inclusive ones.  Every wait is bounded: after kWaitLimitNs without progress
+// the status word gets ICX_ETIMEOUT and the tile publishes what it has, so no
+// other tile can wait forever on it.
+template <int NL, int R = 4>
 __device__ uint4 lookback(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+    static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
     unsigned long long* st = tile_states(h);
     const uint32_t tagA = (epoch << 2) | 1u, tagP = (epoch << 2) | 2u;
-    const int c = lane % NL;
-    const uint32_t my_agg = comp(agg, c);
-    unsigned long long* mine = st + (size_t)tile * kStatesPerTile + c;
-    uint32_t excl = 0;
+    uint4 acc = make_uint4(0, 0, 0, 0);
+    if (lane < NL)
+        st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
+                   ((unsigned long long)(tile ? tagA : tagP) << 32) | comp(agg, lane));
     if (tile != 0) {
-        if (lane < NL) st_relaxed(mine, ((unsigned long long)tagA << 32) | my_agg);
-        const unsigned rmask = NL == 1 ? FULL : (0x11111111u << c);
         long long end = tile;
-        bool done = false;
         unsigned long long t0 = 0;
         for (;;) {
-            const long long p = end - 1 - lane / NL;
-            uint32_t flag = 2, val = 0;
-            if (!done && p >= 0) {
-                const unsigned long long s = ld_relaxed(st + (size_t)p * kStatesPerTile + c);
-                const uint32_t hw = (uint32_t)(s >> 32);
-                val = (uint32_t)s;
-                flag = hw == tagP ? 2u : hw == tagA ? 1u : 0u;
+            uint32_t flag[R];
+            uint4 val[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const long long p = end - 1 - lane - 32 * r;
+                flag[r] = 2;
+                val[r] = make_uint4(0, 0, 0, 0);
+                if (p >= 0) {
+                    const unsigned long long* sp = st + (size_t)p * kStatesPerTile;
+                    if (NL == 1) {
+                        const unsigned long long s0 = ld_relaxed(sp);
+                        const uint32_t t = (uint32_t)(s0 >> 32);
+                        flag[r] = t == tagP ? 2u : t == tagA ? 1u : 0u;
+                        val[r].x = (uint32_t)s0;
+                    } else {
+                        unsigned long long s0, s1, s2, s3;
+                        ld_relaxed_v2(sp, s0, s1);
+                        ld_relaxed_v2(sp + 2, s2, s3);
+                        const uint32_t t = (uint32_t)(s0 >> 32);
+                        const bool same = (uint32_t)(s1 >> 32) == t && (uint32_t)(s2 >> 32) == t &&
+                                          (uint32_t)(s3 >> 32) == t;
+                        flag[r] = !same ? 0u : t == tagP ? 2u : t == tagA ? 1u : 0u;
+                        val[r] = make_uint4((uint32_t)s0, (uint32_t)s1, (uint32_t)s2, (uint32_t)s3);
+                    }
+                }
             }
-            const unsigned pm = __ballot_sync(FULL, flag == 2) & rmask;
-            const unsigned xm = __ballot_sync(FULL, flag == 0) & rmask;
-            const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 32u;
-            const unsigned upto = first >= 31 ? FULL : ((2u << first) - 1u);
-            const bool wait = (xm & upto) != 0;
-            if (__any_sync(FULL, wait)) {
+            // nearest inclusive prefix at distance lane + 32r
+            bool wait = false, found = false;
+            uint4 c = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (found) continue;
+                const unsigned pm = __ballot_sync(FULL, flag[r] == 2);
+                const unsigned xm = __ballot_sync(FULL, flag[r] == 0);
+                const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 32u;
+                const unsigned upto = first >= 31 ? FULL : ((2u << first) - 1u);
+                if (xm & upto) wait = true;
+                if ((unsigned)lane <= first) c = add4(c, val[r]);
+                if (first < 32) found = true;
+            }
+            if (wait) {
                 if (t0 == 0) t0 = globaltimer();
                 if (globaltimer() - t0 > kWaitLimitNs) {
                     if (lane == 0) set_error(h, ICX_ETIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
                 continue;
             }
             t0 = 0;
-            uint32_t contrib = ((unsigned)lane <= first) ? val : 0u;
-#pragma unroll
-            for (int off = 16; off >= NL; off >>= 1) contrib += __shfl_xor_sync(FULL, contrib, off);
-            if (!done) excl += contrib;
-            if (first < 32) done = true;
-            if (__all_sync(FULL, done)) break;
-            end -= 32 / NL;
+            acc = add4(acc, c);
+            if (found) break;
+            end -= 32 * R;
         }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(FULL, acc.x, off);
+            if (NL == 4) {
+                acc.y += __shfl_xor_sync(FULL, acc.y, off);
+                acc.z += __shfl_xor_sync(FULL, acc.z, off);
+                acc.w += __shfl_xor_sync(FULL, acc.w, off);
+            }
+        }
+        if (lane < NL)
+            st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
+                       ((unsigned long long)tagP << 32) | (comp(acc, lane) + comp(agg, lane)));
     }
-    if (lane < NL) st_relaxed(mine, ((unsigned long long)tagP << 32) | (excl + my_agg));
-    uint4 r;
-    r.x = __shfl_sync(FULL, excl, 0);
-    r.y = NL > 1 ? __shfl_sync(FULL, excl, 1) : 0u;
-    r.z = NL > 1 ? __shfl_sync(FULL, excl, 2) : 0u;
-    r.w = NL > 1 ? __shfl_sync(FULL, excl, 3) : 0u;
-    return r;
+    return acc;
 }
 
 // Epoch of this launch (constant while it runs).

@@ -212,14 +212,16 @@ constexpr int kUnitMax = 16 * 16 * 32;  // packed bytes of 16 blocks at width 32
 constexpr int kFBuf = kUnitMax + 128;
 
 struct FpSmem {
+    TileShared t;
     uint64_t bar[kWarps];
     BlockMeta m[kWarps][16];
     uint8_t blk_of[kWarps][16 * 128];  // block of the unit's q-th exception
 };
 
-// Each warp is an independent pipeline over units of 16 blocks (the same
-// structure as the SIMD-BP128 decoder); the next unit's block records and
-// page offsets are loaded while the current unit's copy is in flight.
+// A CTA of kWarps warps takes tiles of kWarps consecutive units of 16 blocks
+// (then the Variable Byte tail), one look-back per tile, exactly like the
+// SIMD-BP128 decoder: per warp its unit's block records, one bulk copy of
+// its packed low bits, unpack, exception patch, local scan.
 template <int DELTA>
 __global__ void __launch_bounds__(kWarps * 32, 2)
     fastpfor_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
@@ -237,62 +239,60 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     const size_t nb = n / 128;
     const uint32_t U = (uint32_t)((nb + 15) / 16);  // units of 16 blocks
     const uint32_t P = (uint32_t)((nb + kBlocksPerPage - 1) / kBlocksPerPage);
-    const uint32_t units = U + 1;                   // then the Variable Byte tail
+    const uint32_t ntiles = (U + 1 + kWarps - 1) / kWarps;  // then the Variable Byte tail
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
-    __syncwarp();
+    __syncthreads();
     uint32_t phase = 0;
 
-    // next unit's records: lane 0 its page base, page flag and packed region,
+    // records of a unit: lane 0 its page base, page flag and packed region,
     // lanes 0..15 its block records
-    uint64_t pbase_n = 0;
-    uint2 um_n = make_uint2(0, 0);
-    uint32_t bad_n = 0;
-    uint4 mrec_n = make_uint4(0, 0, 0, 0);
-    auto prefetch = [&](uint32_t uu) {
-        if (uu < U) {
+    struct Rec {
+        uint64_t pbase;
+        uint2 um;
+        uint32_t bad;
+        uint4 mrec;
+    };
+    auto prefetch = [&](uint32_t t, Rec& r) {
+        const uint32_t uu = t * kWarps + warp;
+        if (t < ntiles && uu < U) {
             const uint32_t p = uu / kUnitsPerPage;
             const uint32_t K = (uint32_t)min((size_t)16, nb - 16 * (size_t)uu);
             if (lane == 0) {
-                pbase_n = index[p];
-                um_n = umeta[uu];
-                bad_n = pmeta[kPageMetaWords * p + 32];
+                r.pbase = index[p];
+                r.um = umeta[uu];
+                r.bad = pmeta[kPageMetaWords * p + 32];
             }
-            if ((uint32_t)lane < K) mrec_n = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
+            if ((uint32_t)lane < K) r.mrec = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
         }
     };
-    // publishes the prefetched records and starts the unit's bulk copy;
-    // returns 0 = nothing to wait for, 1 = copy in flight, 2 = bad page
-    auto issue = [&](uint32_t uu) -> uint32_t {
-        uint32_t r = 0;
-        if (uu < U) {
-            if (lane < 16) reinterpret_cast<uint4*>(m)[lane] = mrec_n;
+    // publishes the records and starts the bulk copy; returns 0 = nothing to
+    // wait for, 1 = copy in flight, 2 = bad page
+    auto issue = [&](uint32_t t, const Rec& r) -> uint32_t {
+        uint32_t res = 0;
+        const uint32_t uu = t * kWarps + warp;
+        if (t < ntiles && uu < U) {
+            if (lane < 16) reinterpret_cast<uint4*>(m)[lane] = r.mrec;
             __syncwarp();
             if (lane == 0) {
-                if (bad_n) {
-                    r = 2;
-                } else if (um_n.y) {
+                if (r.bad) {
+                    res = 2;
+                } else if (r.um.y) {
                     fence_proxy_async();
-                    mbar_expect_tx(bar, um_n.y);
-                    bulk_load(buf, in + pbase_n + um_n.x, um_n.y, bar);
-                    r = 1;
+                    mbar_expect_tx(bar, r.um.y);
+                    bulk_load(buf, in + r.pbase + r.um.x, r.um.y, bar);
+                    res = 1;
                 }
             }
         }
-        return __shfl_sync(FULL, r, 0);
+        return __shfl_sync(FULL, res, 0);
     };
 
-    uint32_t u = warp_grab(h);
-    prefetch(u);
-    uint64_t pbase = __shfl_sync(FULL, pbase_n, 0);
-    uint32_t st = issue(u);
-    uint32_t grabbed = 0;
-    if (lane == 0) grabbed = atomicAdd(&h->tile_counter, 1u);
-    while (u < units) {
-        const uint32_t un = __shfl_sync(FULL, grabbed, 0);
-        prefetch(un);
-        if (lane == 0) grabbed = atomicAdd(&h->tile_counter, 1u);
+    for (;;) {
+        const uint32_t tile = next_tile(S.t, h);
+        if (tile >= ntiles) break;
+        const uint32_t u = tile * kWarps + warp;
         uint4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
@@ -300,6 +300,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         if (u < U) {
             K = (uint32_t)min((size_t)16, nb - 16 * (size_t)u);
             const uint32_t* pg = pmeta + kPageMetaWords * (u / kUnitsPerPage);
+            Rec r{};
+            prefetch(tile, r);
+            const uint64_t pbase = __shfl_sync(FULL, r.pbase, 0);
+            const uint32_t st = issue(tile, r);
             bool ok = st != 2;
             if (!ok) {
                 if (lane == 0) set_error(h, ICX_ECORRUPT);
@@ -400,15 +404,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 K = 1;
             }
         }
-        __syncwarp();  // buffer and records of unit u are no longer read
-        const uint64_t pbase_next = __shfl_sync(FULL, pbase_n, 0);
-        const uint32_t st_n = issue(un);
-        const uint4 agg = unit_local_scan<DELTA>(v, K, false, lane);
-        const uint4 pref = warp_unit_prefix<DELTA>(agg, u, epoch, h);
-        store_unit(out, u < U ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
-        u = un;
-        st = st_n;
-        pbase = pbase_next;
+        __syncwarp();
+        uint4 agg;
+        if (DELTA == ICX_DELTA_4)
+            agg = unit_scan_d4_smem(v, buf32, lane);
+        else
+            agg = unit_local_scan<DELTA>(v, K, false, lane);
+        const uint4 pref = tile_prefix<DELTA>(S.t, agg, tile, epoch, h, warp, lane);
+        if (u <= U) store_unit(out, u < U ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
+        if (DELTA == ICX_DELTA_NONE) __syncthreads();
     }
     finish_launch(h, epoch);
 }

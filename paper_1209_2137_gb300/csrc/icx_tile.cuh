@@ -11,13 +11,16 @@
 
 namespace icx {
 
-constexpr int kWarps = 8;
+constexpr int kWarps = 8;     // default warps per CTA
+constexpr int kMaxWarps = 16;
 
+// Shared state of a CTA tile (sized for the largest CTA).
 struct TileShared {
-    uint4 agg[kWarps];
-    uint4 pref[kWarps];
+    uint4 agg[kMaxWarps];
+    uint4 pref[kMaxWarps];
     uint32_t tile;
-    uint32_t pad[3];
+    uint32_t next;
+    uint32_t pad[2];
 };
 
 // Local scan of a unit held in row ownership (lane t: integers 128k + 4t..+3
@@ -26,12 +29,40 @@ struct TileShared {
 // (stride 1: .x; stride 4: one per residue).
 template <int DELTA>
 __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, bool residue, int lane) {
+    // The 16 blocks' scans are independent except for the carry between
+    // blocks, so every step runs across all blocks before the next step
+    // (16 independent shuffles in flight instead of one dependent chain).
     uint4 agg = make_uint4(0, 0, 0, 0);
     if (DELTA == ICX_DELTA_4 && residue) {
+        // W32 residue ownership: serial over m, then a 3-step scan over the
+        // 8 groups, then the block carries, then back to row ownership.
+        uint32_t incl[16], tot[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[k].y += v[k].x;
+            v[k].z += v[k].y;
+            v[k].w += v[k].z;
+            incl[k] = v[k].w;
+        }
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t y = __shfl_up_sync(FULL, incl[k], off);
+                if (lane >= off) incl[k] += y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tot[k] = __shfl_sync(FULL, incl[k], 28 + (lane & 3));
         uint32_t carry = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if ((uint32_t)k < K) v[k] = residue_to_row(residue_scan_d4(v[k], carry, lane), lane);
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t add = carry + incl[k] - v[k].w;
+            v[k] = make_uint4(v[k].x + add, v[k].y + add, v[k].z + add, v[k].w + add);
+            if ((uint32_t)k < K) carry += tot[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = residue_to_row(v[k], lane);
         agg.x = __shfl_sync(FULL, carry, 0);
         agg.y = __shfl_sync(FULL, carry, 1);
         agg.z = __shfl_sync(FULL, carry, 2);
@@ -40,14 +71,34 @@ __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, boo
     }
     if (residue) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if ((uint32_t)k < K) v[k] = residue_to_row(v[k], lane);
+        for (int k = 0; k < 16; ++k) v[k] = residue_to_row(v[k], lane);
     }
     if (DELTA == ICX_DELTA_1) {
+        uint32_t incl[16], tot[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[k].y += v[k].x;
+            v[k].z += v[k].y;
+            v[k].w += v[k].z;
+            incl[k] = v[k].w;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t y = __shfl_up_sync(FULL, incl[k], off);
+                if (lane >= off) incl[k] += y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tot[k] = __shfl_sync(FULL, incl[k], 31);
         uint32_t carry = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if ((uint32_t)k < K) v[k] = row_scan_d1(v[k], carry, lane);
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t add = carry + incl[k] - v[k].w;
+            v[k] = make_uint4(v[k].x + add, v[k].y + add, v[k].z + add, v[k].w + add);
+            carry += tot[k];
+        }
         agg.x = carry;
     } else if (DELTA == ICX_DELTA_4) {
         uint4 carry = make_uint4(0, 0, 0, 0);
@@ -59,28 +110,78 @@ __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, boo
     return agg;
 }
 
+// Stride-4 scan of a whole unit in row ownership through an 8 KB shared
+// scratch (the warp's staging buffer, free after unpacking): the 16 x 32 x 4
+// values are written in position order, each lane then owns two columns
+// (block k = lane/2, residues 2*(lane&1) and +1) and scans them down the 32
+// rows serially, one shuffle scan over the blocks adds the column carries,
+// and the values are read back in row ownership.  Word (k, t, c) lives at
+// 128k + 4(t ^ (k & 7)) + c, which keeps both the 128-bit row accesses and
+// the 64-bit column accesses free of bank conflicts.  Returns the unit's
+// four residue aggregates.
+__device__ __forceinline__ uint4 unit_scan_d4_smem(uint4 (&v)[16], uint32_t* scratch, int lane) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        *reinterpret_cast<uint4*>(scratch + 128 * k + 4 * (lane ^ (k & 7))) = v[k];
+    __syncwarp();
+    const int k = lane >> 1, c0 = 2 * (lane & 1);
+    uint32_t* col = scratch + 128 * k + c0;
+    uint32_t x[32], y[32];
+    uint32_t sx = 0, sy = 0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        const uint2 e = *reinterpret_cast<const uint2*>(col + 4 * (t ^ (k & 7)));
+        sx += e.x;
+        sy += e.y;
+        x[t] = sx;
+        y[t] = sy;
+    }
+    // carries of the earlier blocks: exclusive scan over k (lanes of one parity)
+    uint32_t ix = sx, iy = sy;
+#pragma unroll
+    for (int off = 2; off < 32; off <<= 1) {
+        const uint32_t a = __shfl_up_sync(FULL, ix, off), b = __shfl_up_sync(FULL, iy, off);
+        if (lane >= off) {
+            ix += a;
+            iy += b;
+        }
+    }
+    const uint32_t ex = ix - sx, ey = iy - sy;
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+        *reinterpret_cast<uint2*>(col + 4 * (t ^ (k & 7))) = make_uint2(x[t] + ex, y[t] + ey);
+    __syncwarp();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+        v[kk] = *reinterpret_cast<const uint4*>(scratch + 128 * kk + 4 * (lane ^ (kk & 7)));
+    const uint4 agg = make_uint4(__shfl_sync(FULL, ix, 30), __shfl_sync(FULL, iy, 30), __shfl_sync(FULL, ix, 31),
+                                 __shfl_sync(FULL, iy, 31));
+    __syncwarp();
+    return agg;
+}
+
 // CTA-wide: exclusive prefix of this warp's unit (tile carry-in from the
 // look-back plus the aggregates of the tile's earlier units).  Contains two
 // __syncthreads; every thread of the CTA must call it.
-template <int DELTA>
+template <int DELTA, int W = kWarps>
 __device__ __forceinline__ uint4 tile_prefix(TileShared& S, uint4 agg, uint32_t tile, uint32_t epoch, WsHeader* h,
                                              int warp, int lane) {
     if (DELTA == ICX_DELTA_NONE) return make_uint4(0, 0, 0, 0);
     if (lane == 0) S.agg[warp] = agg;
     __syncthreads();
     if (warp == 0) {
-        const uint4 mine = lane < kWarps ? S.agg[lane] : make_uint4(0, 0, 0, 0);
+        const uint4 mine = lane < W ? S.agg[lane] : make_uint4(0, 0, 0, 0);
         uint4 incl = mine;
 #pragma unroll
-        for (int off = 1; off < kWarps; off <<= 1) {
+        for (int off = 1; off < W; off <<= 1) {
             uint4 y = make_uint4(__shfl_up_sync(FULL, incl.x, off), __shfl_up_sync(FULL, incl.y, off),
                                  __shfl_up_sync(FULL, incl.z, off), __shfl_up_sync(FULL, incl.w, off));
             if (lane >= off) incl = add4(incl, y);
         }
-        const uint4 total = shfl4(incl, kWarps - 1);
+        const uint4 total = shfl4(incl, W - 1);
         const uint4 base = DELTA == ICX_DELTA_1 ? lookback<1>(h, epoch, tile, total)
                                                 : lookback<4>(h, epoch, tile, total);
-        if (lane < kWarps) S.pref[lane] = add4(base, sub4(incl, mine));
+        if (lane < W) S.pref[lane] = add4(base, sub4(incl, mine));
     }
     __syncthreads();
     uint4 pref = S.pref[warp];

@@ -145,3 +145,40 @@ def workload_clustered_long(seed: int = SEED_BASE + 20) -> np.ndarray:
 
 def workload_exceptions(n: int = 1 << 26, seed: int = SEED_BASE + 3) -> np.ndarray:
     return exception_heavy(n, seed)
+
+
+def posting_lists(nlists: int = 65536, total: int = 1 << 28, lo: int = 128, hi: int = 1 << 22,
+                  alpha: float = 1.1, reading: str = "A", seed: int = SEED_BASE + 4):
+    """Posting-list-like batch: list lengths Zipf(alpha) over [lo, hi].
+
+    Reading "A": lengths drawn i.i.d. with P(L) ~ L^-alpha on [lo, hi]
+    (inverse CDF of the continuous law, floored), then scaled by total/sum and
+    clamped to [lo, hi].  Reading "B": rank-size L_r = hi * r^-alpha, clamped
+    at lo.  Per list: beta uniform in {1..20} (the mean-delta bits), range
+    R = min(L * 2^beta, 2^32), L distinct values uniform in [0, R), sorted;
+    a coin picks the codec (True = SIMD-BP128 with stride-4 deltas, False =
+    SIMD-FastPFOR with stride-1 deltas).
+
+    Returns (lengths, offsets, values, bp128_mask)."""
+    z = splitmix64(seed, 0, 3 * nlists)
+    u = ((z[:nlists] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+    if reading == "A":
+        a1 = 1.0 - alpha
+        lo_p, hi_p = lo ** a1, hi ** a1
+        L = np.floor((lo_p + u * (hi_p - lo_p)) ** (1.0 / a1))
+        L = np.clip(np.floor(L * (total / L.sum())), lo, hi).astype(np.int64)
+    elif reading == "B":
+        r = np.arange(1, nlists + 1, dtype=np.float64)
+        L = np.maximum(lo, np.round(hi * r ** (-alpha))).astype(np.int64)
+    else:
+        raise ValueError(reading)
+    beta = 1 + (z[nlists:2 * nlists] % np.uint64(20)).astype(np.int64)
+    bp = ((z[2 * nlists:] >> np.uint64(40)) & np.uint64(1)).astype(bool)
+    offsets = np.zeros(nlists + 1, dtype=np.int64)
+    np.cumsum(L, out=offsets[1:])
+    values = np.empty(int(offsets[-1]), dtype=np.uint32)
+    for i in range(nlists):
+        n = int(L[i])
+        R = min(n << int(beta[i]), 1 << 32)
+        values[offsets[i]:offsets[i + 1]] = distinct_sorted(n, R, seed * 1000003 + i)
+    return L, offsets, values, bp
