@@ -207,6 +207,8 @@ def run_gpu(args, world, rank, local):
     icx.lib()  # fails loudly if the CUDA library is missing
     if args.bp128_warps:
         icx.set_tuning("bp128.warps_per_cta", args.bp128_warps)
+    if args.bp128_l2_prefetch >= 0:
+        icx.set_tuning("bp128.l2_prefetch", args.bp128_l2_prefetch)
     arrays = workload_arrays(args.n)
     stream = torch.cuda.current_stream()
 
@@ -463,6 +465,7 @@ def main():
     ap.add_argument("--extra-none", action="store_true", help="also time decodes without differential decoding")
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
+    ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

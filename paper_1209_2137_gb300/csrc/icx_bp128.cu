@@ -50,15 +50,20 @@ __device__ __forceinline__ uint4 unpack_block(const uint8_t* buf, uint32_t base_
 
 // A CTA of W warps takes tiles of W consecutive units (unit u < M is
 // metablock u, unit M the Variable Byte tail); tile ids come from the
-// launch's counter when the CTA starts on them, so every tile that exists is
-// being worked on (the look-back never waits on an idle tile).  Per warp:
-// one bulk copy of its metablock into its shared buffer, unpack into
-// registers (64 integers per lane), local scan; then one look-back per tile
-// and 128-bit stores.
+// launch's counter.  Per tile:
+//   1. every warp waits for its metablock (one bulk copy into its shared
+//      buffer), unpacks it into registers (64 integers per lane) and sums it;
+//   2. warp 0 publishes the tile aggregate at once, so that the look-backs of
+//      later tiles never wait for this tile's local scans;
+//   3. every warp scans its unit locally while warp 0 resolves the tile's
+//      carry-in (decoupled look-back) and takes the next tile id;
+//   4. every warp starts the bulk copy of its next metablock, then adds its
+//      carry and stores (the copy lands during the stores).
 template <int DELTA, int FMT, int W>
 __global__ void __launch_bounds__(W * 32, 16 / W)
     bp128_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out,
-                        size_t n, const uint64_t* __restrict__ index, WsHeader* h) {
+                        size_t n, const uint64_t* __restrict__ index, bool l2_ahead, WsHeader* h) {
+    constexpr int NL = DELTA == ICX_DELTA_4 ? 4 : 1;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -70,41 +75,61 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
+    if (threadIdx.x == 0) S.nx[0] = atomicAdd(&h->tile_counter, 1u);
     __syncthreads();
-    uint32_t phase = 0;
+    uint32_t phase = 0, it = 0;
+    bool broken = false;  // a copy of this warp never landed: decode nothing more
+    // starts the bulk copy of metablock uu; returns its size, ~0u for an
+    // invalid index entry, 0 if there is nothing to copy
+    auto issue = [&](uint32_t uu) -> uint32_t {
+        uint32_t size = 0;
+        if (uu < M && !broken && lane == 0) {
+            const uint64_t off = index[uu], end = index[uu + 1];
+            const bool ok = off <= end && end <= in_bytes && end - off >= 16 && end - off <= kMetaMax &&
+                            ((off | end) & 15) == 0;
+            size = ok ? (uint32_t)(end - off) : ~0u;
+            if (ok) {
+                fence_proxy_async();
+                mbar_expect_tx(bar, size);
+                bulk_load(buf, in + off, size, bar);
+            }
+        }
+        return __shfl_sync(FULL, size, 0);
+    };
+    uint32_t tile = S.nx[0];
+    uint32_t size = tile < ntiles ? issue(tile * W + warp) : 0u;
 
-    for (;;) {
-        const uint32_t tile = next_tile(S, h);
-        if (tile >= ntiles) break;
+    while (tile < ntiles) {
         const uint32_t u = tile * W + warp;
         uint4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
         uint32_t K = 0;        // blocks in this unit
         bool residue = false;  // W32 metablocks arrive in residue ownership
+        // the metablock one grid of tiles ahead: some CTA takes it about one
+        // tile-time from now; bring it into L2 so that its copy is short
+        const uint32_t ahead = u + gridDim.x * W;
+        uint64_t pf_off = 0, pf_end = 0;
+        if (l2_ahead && lane == 0 && ahead < M) {
+            pf_off = __ldg(index + ahead);
+            pf_end = __ldg(index + ahead + 1);
+        }
         if (u < M) {
             K = (uint32_t)min((size_t)16, nb - 16 * (size_t)u);
-            uint32_t size = 0;
-            if (lane == 0) {
-                const uint64_t off = index[u], end = index[u + 1];
-                const bool ok = off <= end && end <= in_bytes && end - off >= 16 && end - off <= kMetaMax &&
-                                ((off | end) & 15) == 0;
-                size = ok ? (uint32_t)(end - off) : ~0u;
-                if (ok) {
-                    fence_proxy_async();
-                    mbar_expect_tx(bar, size);
-                    bulk_load(buf, in + off, size, bar);
-                }
-            }
-            size = __shfl_sync(FULL, size, 0);
-            bool ok = size != ~0u;
-            if (!ok) {
+            bool ok = size != ~0u && !broken;
+            if (size == ~0u) {
                 if (lane == 0) set_error(h, ICX_ECORRUPT);
-            } else {
+            } else if (ok) {
                 ok = __all_sync(FULL, mbar_wait(bar, phase));
                 phase ^= 1;
-                if (!ok && lane == 0) set_error(h, ICX_ETIMEOUT);
+                if (!ok) {
+                    broken = true;
+                    if (lane == 0) set_error(h, ICX_ETIMEOUT);
+                }
             }
+            if (lane == 0 && pf_off < pf_end && pf_end <= in_bytes && pf_end - pf_off <= kMetaMax &&
+                ((pf_off | pf_end) & 15) == 0)
+                prefetch_l2(in + pf_off, (uint32_t)(pf_end - pf_off));
             if (ok) {
                 const uint4 desc = *reinterpret_cast<const uint4*>(buf);
                 uint32_t sum = 0, maxw = 0;
@@ -143,15 +168,40 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
                 K = 1;
             }
         }
-        uint4 agg;
+        uint4 mine = make_uint4(0, 0, 0, 0), incl = mine;
+        if (DELTA != ICX_DELTA_NONE) {
+            const uint4 agg = unit_sum<DELTA>(v, residue);
+            if (lane == 0) S.agg[warp] = agg;
+            __syncthreads();
+            if (warp == 0) {
+                incl = tile_agg_scan<W>(S, mine, lane);
+                lookback_publish<NL>(h, epoch, tile, shfl4(incl, W - 1));
+            }
+        }
         if (DELTA == ICX_DELTA_4 && FMT == ICX_FMT_PAPER)
-            agg = unit_scan_d4_smem(v, reinterpret_cast<uint32_t*>(buf), lane);
+            unit_scan_d4_smem(v, reinterpret_cast<uint32_t*>(buf), lane);
         else
-            agg = unit_local_scan<DELTA>(v, K, residue, lane);
-        const uint4 pref = tile_prefix<DELTA, W>(S, agg, tile, epoch, h, warp, lane);
+            unit_local_scan<DELTA>(v, K, residue, lane);
+        if (DELTA != ICX_DELTA_NONE && warp == 0) {
+            const uint4 base = lookback_resolve<NL>(h, epoch, tile, shfl4(incl, W - 1));
+            if (lane < W) S.pref[lane] = add4(base, sub4(incl, mine));
+        }
+        ++it;
+        if (threadIdx.x == 0) S.nx[it & 1] = atomicAdd(&h->tile_counter, 1u);
+        __syncthreads();
+        uint4 pref = make_uint4(0, 0, 0, 0);
+        if (DELTA != ICX_DELTA_NONE) {
+            pref = S.pref[warp];
+            if (DELTA == ICX_DELTA_1) pref = make_uint4(pref.x, pref.x, pref.x, pref.x);
+        }
+        const uint32_t next = S.nx[it & 1];
+        __syncwarp();
+        size = next < ntiles ? issue(next * W + warp) : 0u;  // lands during the stores
         if (u <= M) store_unit(out, u < M ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
-        if (DELTA == ICX_DELTA_NONE) __syncthreads();  // S.tile is rewritten next iteration
+        tile = next;
     }
+    // a copy that never landed must not outlive the CTA's shared memory
+    if (broken) mbar_wait(bar, phase);
     finish_launch(h, epoch);
 }
 
@@ -227,6 +277,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 
 // ------------------------------------------------------------ launchers
 
+static int g_bp128_warps = 0;          // warps per CTA of the SIMD-BP128 decoder (0 = per-stride default)
+static bool g_bp128_l2_ahead = true;  // L2 prefetch one grid of tiles ahead
+
 template <int DELTA, int FMT, int W>
 static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                 const uint64_t* index, WsHeader* h, cudaStream_t s) {
@@ -247,7 +300,7 @@ static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* ou
     const size_t M = (n / 128 + 15) / 16;
     const size_t ctas = (M + 1 + W - 1) / W;
     const int grid = (int)min((size_t)blocks_per_sm * sms, ctas);
-    kern<<<grid, W * 32, smem, s>>>(in, in_bytes, out, n, index, h);
+    kern<<<grid, W * 32, smem, s>>>(in, in_bytes, out, n, index, g_bp128_l2_ahead, h);
     return cudaGetLastError();
 }
 
@@ -258,9 +311,12 @@ static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* ou
 
 
 
-static int g_bp128_warps = 0;  // warps per CTA of the SIMD-BP128 decoder (0 = per-stride default)
+  // warps per CTA of the SIMD-BP128 decoder (0 = per-stride default)
 
 void set_bp128_warps(int w) { g_bp128_warps = (w == 4 || w == 8 || w == 16) ? w : 0; }
+
+
+void set_bp128_prefetch(int on) { g_bp128_l2_ahead = on != 0; }
 
 template <int DELTA, int FMT>
 static cudaError_t launch_bp128_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,

@@ -122,6 +122,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Hint: bring `bytes` (a multiple of 16) at the 16-byte aligned `src` into L2.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -281,88 +286,106 @@ __device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsig
 // inclusive ones.  Every wait is bounded: after kWaitLimitNs without progress
 // the status word gets ICX_ETIMEOUT and the tile publishes what it has, so no
 // other tile can wait forever on it.
+// Publishes a tile's aggregate (the first tile publishes it as its inclusive
+// prefix).  Lanes 0..NL-1 of the calling warp store one chain each.
+template <int NL>
+__device__ __forceinline__ void lookback_publish(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t tag = (epoch << 2) | (tile ? 1u : 2u);
+    if (lane < NL)
+        st_relaxed(tile_states(h) + (size_t)tile * kStatesPerTile + lane,
+                   ((unsigned long long)tag << 32) | comp(agg, lane));
+}
+
+// Resolves the exclusive prefix of `tile` (whose aggregate `agg` is already
+// published) from its predecessors' states and publishes its inclusive
+// prefix.  Whole warp.
 template <int NL, int R = 4>
-__device__ uint4 lookback(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+__device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
     static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
     unsigned long long* st = tile_states(h);
     const uint32_t tagA = (epoch << 2) | 1u, tagP = (epoch << 2) | 2u;
     uint4 acc = make_uint4(0, 0, 0, 0);
+    if (tile == 0) return acc;
+    long long end = tile;
+    unsigned long long t0 = 0;
+    for (;;) {
+        uint32_t flag[R];
+        uint4 val[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long p = end - 1 - lane - 32 * r;
+            flag[r] = 2;
+            val[r] = make_uint4(0, 0, 0, 0);
+            if (p >= 0) {
+                const unsigned long long* sp = st + (size_t)p * kStatesPerTile;
+                if (NL == 1) {
+                    const unsigned long long s0 = ld_relaxed(sp);
+                    const uint32_t t = (uint32_t)(s0 >> 32);
+                    flag[r] = t == tagP ? 2u : t == tagA ? 1u : 0u;
+                    val[r].x = (uint32_t)s0;
+                } else {
+                    unsigned long long s0, s1, s2, s3;
+                    ld_relaxed_v2(sp, s0, s1);
+                    ld_relaxed_v2(sp + 2, s2, s3);
+                    const uint32_t t = (uint32_t)(s0 >> 32);
+                    const bool same = (uint32_t)(s1 >> 32) == t && (uint32_t)(s2 >> 32) == t &&
+                                      (uint32_t)(s3 >> 32) == t;
+                    flag[r] = !same ? 0u : t == tagP ? 2u : t == tagA ? 1u : 0u;
+                    val[r] = make_uint4((uint32_t)s0, (uint32_t)s1, (uint32_t)s2, (uint32_t)s3);
+                }
+            }
+        }
+        // nearest inclusive prefix at distance lane + 32r
+        bool wait = false, found = false;
+        uint4 c = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (found) continue;
+            const unsigned pm = __ballot_sync(FULL, flag[r] == 2);
+            const unsigned xm = __ballot_sync(FULL, flag[r] == 0);
+            const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 32u;
+            const unsigned upto = first >= 31 ? FULL : ((2u << first) - 1u);
+            if (xm & upto) wait = true;
+            if ((unsigned)lane <= first) c = add4(c, val[r]);
+            if (first < 32) found = true;
+        }
+        if (wait) {
+            if (t0 == 0) t0 = globaltimer();
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                if (lane == 0) set_error(h, ICX_ETIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        t0 = 0;
+        acc = add4(acc, c);
+        if (found) break;
+        end -= 32 * R;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        acc.x += __shfl_xor_sync(FULL, acc.x, off);
+        if (NL == 4) {
+            acc.y += __shfl_xor_sync(FULL, acc.y, off);
+            acc.z += __shfl_xor_sync(FULL, acc.z, off);
+            acc.w += __shfl_xor_sync(FULL, acc.w, off);
+        }
+    }
     if (lane < NL)
         st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
-                   ((unsigned long long)(tile ? tagA : tagP) << 32) | comp(agg, lane));
-    if (tile != 0) {
-        long long end = tile;
-        unsigned long long t0 = 0;
-        for (;;) {
-            uint32_t flag[R];
-            uint4 val[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const long long p = end - 1 - lane - 32 * r;
-                flag[r] = 2;
-                val[r] = make_uint4(0, 0, 0, 0);
-                if (p >= 0) {
-                    const unsigned long long* sp = st + (size_t)p * kStatesPerTile;
-                    if (NL == 1) {
-                        const unsigned long long s0 = ld_relaxed(sp);
-                        const uint32_t t = (uint32_t)(s0 >> 32);
-                        flag[r] = t == tagP ? 2u : t == tagA ? 1u : 0u;
-                        val[r].x = (uint32_t)s0;
-                    } else {
-                        unsigned long long s0, s1, s2, s3;
-                        ld_relaxed_v2(sp, s0, s1);
-                        ld_relaxed_v2(sp + 2, s2, s3);
-                        const uint32_t t = (uint32_t)(s0 >> 32);
-                        const bool same = (uint32_t)(s1 >> 32) == t && (uint32_t)(s2 >> 32) == t &&
-                                          (uint32_t)(s3 >> 32) == t;
-                        flag[r] = !same ? 0u : t == tagP ? 2u : t == tagA ? 1u : 0u;
-                        val[r] = make_uint4((uint32_t)s0, (uint32_t)s1, (uint32_t)s2, (uint32_t)s3);
-                    }
-                }
-            }
-            // nearest inclusive prefix at distance lane + 32r
-            bool wait = false, found = false;
-            uint4 c = make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (found) continue;
-                const unsigned pm = __ballot_sync(FULL, flag[r] == 2);
-                const unsigned xm = __ballot_sync(FULL, flag[r] == 0);
-                const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 32u;
-                const unsigned upto = first >= 31 ? FULL : ((2u << first) - 1u);
-                if (xm & upto) wait = true;
-                if ((unsigned)lane <= first) c = add4(c, val[r]);
-                if (first < 32) found = true;
-            }
-            if (wait) {
-                if (t0 == 0) t0 = globaltimer();
-                if (globaltimer() - t0 > kWaitLimitNs) {
-                    if (lane == 0) set_error(h, ICX_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
-                continue;
-            }
-            t0 = 0;
-            acc = add4(acc, c);
-            if (found) break;
-            end -= 32 * R;
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(FULL, acc.x, off);
-            if (NL == 4) {
-                acc.y += __shfl_xor_sync(FULL, acc.y, off);
-                acc.z += __shfl_xor_sync(FULL, acc.z, off);
-                acc.w += __shfl_xor_sync(FULL, acc.w, off);
-            }
-        }
-        if (lane < NL)
-            st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
-                       ((unsigned long long)tagP << 32) | (comp(acc, lane) + comp(agg, lane)));
-    }
+                   ((unsigned long long)tagP << 32) | (comp(acc, lane) + comp(agg, lane)));
     return acc;
+}
+
+// Decoupled look-back of one tile: publish its aggregate, resolve its
+// exclusive prefix, publish its inclusive prefix.  Whole warp.
+template <int NL, int R = 4>
+__device__ __forceinline__ uint4 lookback(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+    lookback_publish<NL>(h, epoch, tile, agg);
+    return lookback_resolve<NL, R>(h, epoch, tile, agg);
 }
 
 // Epoch of this launch (constant while it runs).

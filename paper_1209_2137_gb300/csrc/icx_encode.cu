@@ -54,7 +54,7 @@ __device__ __forceinline__ uint4 row_deltas(const uint32_t* __restrict__ x, size
 template <int DELTA>
 __device__ __forceinline__ uint32_t delta_at(const uint32_t* __restrict__ x, size_t p) {
     if (DELTA == ICX_DELTA_NONE) return x[p];
-    const uint32_t prev = p >= (size_t)DELTA ? x[p - DELTA] : 0u;
+    const uint32_t prev = (DELTA > 0 && p >= (size_t)DELTA) ? x[p - DELTA] : 0u;
     return x[p] - prev;
 }
 

@@ -20,7 +20,7 @@ struct TileShared {
     uint4 pref[kMaxWarps];
     uint32_t tile;
     uint32_t next;
-    uint32_t pad[2];
+    uint32_t nx[2];  // next tile id, double-buffered by iteration parity
 };
 
 // Local scan of a unit held in row ownership (lane t: integers 128k + 4t..+3
@@ -108,6 +108,58 @@ __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, boo
         agg = carry;
     }
     return agg;
+}
+
+// Aggregate of a unit straight after unpacking (before its local scan):
+// stride 1: the sum of all its deltas in .x; stride 4: one sum per residue
+// mod 4.  In row ownership (lane t: integers 4t..4t+3 of every block)
+// component c is residue c; in W32 residue ownership lane j holds residue
+// j & 3 in all four components.
+template <int DELTA>
+__device__ __forceinline__ uint4 unit_sum(const uint4 (&v)[16], bool residue) {
+    if constexpr (DELTA == ICX_DELTA_NONE) {
+        return make_uint4(0, 0, 0, 0);
+    } else {
+        uint4 s = v[0];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) s = add4(s, v[k]);
+        uint32_t t = s.x + s.y + s.z + s.w;
+        if constexpr (DELTA == ICX_DELTA_1) {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+            return make_uint4(t, 0, 0, 0);
+        } else {
+            if (residue) {
+#pragma unroll
+                for (int off = 16; off >= 4; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+                return make_uint4(__shfl_sync(FULL, t, 0), __shfl_sync(FULL, t, 1), __shfl_sync(FULL, t, 2),
+                                  __shfl_sync(FULL, t, 3));
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                s.x += __shfl_xor_sync(FULL, s.x, off);
+                s.y += __shfl_xor_sync(FULL, s.y, off);
+                s.z += __shfl_xor_sync(FULL, s.z, off);
+                s.w += __shfl_xor_sync(FULL, s.w, off);
+            }
+            return s;
+        }
+    }
+}
+
+// Warp 0 of a tile: inclusive scan of the W unit aggregates in S.agg (lane i
+// < W gets unit i), returning the lane's own aggregate in `mine`.
+template <int W>
+__device__ __forceinline__ uint4 tile_agg_scan(const TileShared& S, uint4& mine, int lane) {
+    mine = lane < W ? S.agg[lane] : make_uint4(0, 0, 0, 0);
+    uint4 incl = mine;
+#pragma unroll
+    for (int off = 1; off < W; off <<= 1) {
+        const uint4 y = make_uint4(__shfl_up_sync(FULL, incl.x, off), __shfl_up_sync(FULL, incl.y, off),
+                                   __shfl_up_sync(FULL, incl.z, off), __shfl_up_sync(FULL, incl.w, off));
+        if (lane >= off) incl = add4(incl, y);
+    }
+    return incl;
 }
 
 // Stride-4 scan of a whole unit in row ownership through an 8 KB shared
