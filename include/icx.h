@@ -205,6 +205,86 @@ icx_status icx_set_tuning(const char *key, int value);
 /* Library version string. */
 const char *icx_version(void);
 
+/* ------------------------------------------------------------------------
+ * Batched decoding: many independent arrays ("lists", e.g. posting lists)
+ * of uneven length decoded by one CUDA graph launch.  No counterpart in the
+ * paper, which decodes one array at a time; each list is decoded exactly as
+ * bp128_decode / fastpfor_decode would decode it alone.
+ *
+ * The plan flattens every list into units (a SIMD-BP128 metablock, 16
+ * blocks of a SIMD-FastPFOR page, or the Variable Byte tail) in a work-list;
+ * one persistent kernel walks the work-list in tiles with a segmented
+ * decoupled look-back (the running sum restarts at every list), after one
+ * page-parse launch over every SIMD-FastPFOR page.  Both launches are
+ * captured in one CUDA graph at plan creation.
+ * ---------------------------------------------------------------------- */
+
+typedef enum { ICX_CODEC_BP128 = 0, ICX_CODEC_FASTPFOR = 1 } icx_codec;
+
+/* One list of a batch.  d_in: its stream (16-byte aligned, in_bytes long);
+ * d_out: n integers (16-byte aligned, not overlapping any other list's
+ * output); d_index: its metablock / page index as built by bp128_index,
+ * fastpfor_index or the encoders; it may be NULL where the single-array call
+ * allows it (at most one metablock / page).  delta: icx_delta; fmt:
+ * icx_layout (SIMD-BP128 only, else ignored).  The caller owns all buffers
+ * and keeps them alive and unmodified while the plan is in use. */
+typedef struct {
+    const uint8_t *d_in;
+    size_t in_bytes;
+    uint32_t *d_out;
+    size_t n;
+    const uint64_t *d_index;
+    int codec;
+    int delta;
+    int fmt;
+} icx_list_desc;
+
+/* Launch parameters of a plan.  warps_per_cta: 4 or 8 (0 = tune); order:
+ * work-list order of the lists, 0 = as given, 1 = longest first, 2 =
+ * shortest first (-1 = tune); l2_prefetch: 1/0 (-1 = tune).  Any field left
+ * to tune is chosen by timing the candidates on this plan's own data at
+ * creation (its outputs are written meanwhile); the choice is cached in the
+ * JSON file cache_path (NULL: $ICX_TUNE_CACHE, else no cache) under a key
+ * made from the lists' lengths, codecs and deltas. */
+typedef struct {
+    int warps_per_cta;
+    int order;
+    int l2_prefetch;
+    const char *cache_path;
+} icx_tuning;
+
+typedef struct icx_plan icx_plan;
+
+/* Creates a plan on the current device: validates every list (arguments as
+ * for the single-array calls; ICX_EINVAL / ICX_EALIGN name nothing, see
+ * icx_plan_error_list), allocates the plan's device memory once (work-list,
+ * page records, look-back states: about 8 bytes per 2048 integers plus 0.5
+ * bytes per integer of SIMD-FastPFOR lists), tunes if asked (t NULL = tune
+ * everything) and captures the CUDA graph.  Synchronous. */
+icx_status icx_plan_create(const icx_list_desc *lists, size_t nlists, const icx_tuning *t, icx_plan **plan);
+
+/* Index of the first list that made icx_plan_create fail, or -1. */
+long long icx_plan_error_list(void);
+
+/* Decodes every list: one graph launch on `stream`, asynchronous.  Data
+ * errors go to the plan's status word (icx_plan_status). */
+icx_status icx_plan_launch(icx_plan *plan, icx_stream_t stream);
+
+/* The same lists decoded by one single-array call per list
+ * (bp128_decode / fastpfor_decode, same kernels), all captured in one CUDA
+ * graph at the first call: the baseline of the batched launch. */
+icx_status icx_plan_launch_per_list(icx_plan *plan, icx_stream_t stream);
+
+/* Synchronises `stream`, returns the first data error of the plan's
+ * launches since the last call in *out and clears it. */
+icx_status icx_plan_status(icx_plan *plan, icx_stream_t stream, icx_status *out);
+
+/* The launch parameters in use (after tuning). */
+icx_status icx_plan_tuning(const icx_plan *plan, icx_tuning *out);
+
+/* Frees the plan's device memory and graphs. */
+void icx_plan_destroy(icx_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "ICX_OK", 1: "ICX_EINVAL", 2: "ICX_EALIGN", 3: "ICX_ECORRUPT"
                 5: "ICX_ECUDA", 6: "ICX_ETIMEOUT"}
 DELTA_NONE, DELTA_1, DELTA_4 = 0, 1, 4
 FMT_PAPER, FMT_W32 = 0, 1
+CODEC_BP128, CODEC_FASTPFOR = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -71,6 +72,13 @@ def lib():
                 "fastpfor_encode": ([vp, sz, i, vp, sz, vp, vp, vp, sz, vp], i),
                 "icx_version": ([], ctypes.c_char_p),
                 "icx_set_tuning": ([ctypes.c_char_p, i], i),
+                "icx_plan_create": ([vp, sz, vp, ctypes.POINTER(vp)], i),
+                "icx_plan_error_list": ([], ctypes.c_longlong),
+                "icx_plan_launch": ([vp, vp], i),
+                "icx_plan_launch_per_list": ([vp, vp], i),
+                "icx_plan_status": ([vp, vp, ctypes.POINTER(ctypes.c_int)], i),
+                "icx_plan_tuning": ([vp, vp], i),
+                "icx_plan_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -82,7 +90,9 @@ def lib():
 EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_bytes", "icx_fastpfor_max_bytes",
             "icx_workspace_bytes", "icx_encode_workspace_bytes", "icx_workspace_init", "icx_status_read",
             "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "delta_decode", "delta_encode",
-            "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning")
+            "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning", "icx_plan_create",
+            "icx_plan_error_list", "icx_plan_launch", "icx_plan_launch_per_list", "icx_plan_status", "icx_plan_tuning",
+            "icx_plan_destroy")
 
 
 def _check(code: int, what: str):
@@ -314,3 +324,158 @@ def set_tuning(key: str, value: int) -> None:
 
 def version() -> str:
     return lib().icx_version().decode()
+
+
+# -- batched decoding ----------------------------------------------------------
+
+class ListDesc(ctypes.Structure):
+    """icx_list_desc: one list of a batch."""
+    _fields_ = [("d_in", ctypes.c_void_p), ("in_bytes", ctypes.c_size_t), ("d_out", ctypes.c_void_p),
+                ("n", ctypes.c_size_t), ("d_index", ctypes.c_void_p), ("codec", ctypes.c_int),
+                ("delta", ctypes.c_int), ("fmt", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    """icx_tuning: warps_per_cta 4/8 (0 = tune), order 0/1/2 (-1 = tune),
+    l2_prefetch 1/0 (-1 = tune), cache_path (None: $ICX_TUNE_CACHE)."""
+    _fields_ = [("warps_per_cta", ctypes.c_int), ("order", ctypes.c_int), ("l2_prefetch", ctypes.c_int),
+                ("cache_path", ctypes.c_char_p)]
+
+
+class Plan:
+    """A batch of lists decoded by one CUDA graph launch (icx_plan_*).
+
+    ``descs`` is a sequence of ListDesc; the device buffers they point to must
+    outlive the plan.  ``tuning`` is a Tuning, a dict of its fields, or None
+    (tune everything)."""
+
+    def __init__(self, descs, tuning=None):
+        arr = (ListDesc * len(descs))(*descs)
+        if isinstance(tuning, dict):
+            path = tuning.get("cache_path")
+            tuning = Tuning(tuning.get("warps_per_cta", 0), tuning.get("order", -1), tuning.get("l2_prefetch", -1),
+                            path.encode() if isinstance(path, str) else path)
+        self._keep = (arr, tuning)
+        handle = ctypes.c_void_p()
+        code = lib().icx_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(descs),
+                                     ctypes.cast(ctypes.pointer(tuning), ctypes.c_void_p) if tuning else None,
+                                     ctypes.byref(handle))
+        if code != OK:
+            bad = lib().icx_plan_error_list()
+            raise IcxError(code, "icx_plan_create" + (f" (list {bad})" if bad >= 0 else ""))
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(lib().icx_plan_launch(self._h, _stream(stream)), "icx_plan_launch")
+
+    def launch_per_list(self, stream=None):
+        _check(lib().icx_plan_launch_per_list(self._h, _stream(stream)), "icx_plan_launch_per_list")
+
+    def status(self, stream=None) -> int:
+        st = ctypes.c_int(0)
+        _check(lib().icx_plan_status(self._h, _stream(stream), ctypes.byref(st)), "icx_plan_status")
+        return st.value
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().icx_plan_tuning(self._h, ctypes.cast(ctypes.pointer(t), ctypes.c_void_p)), "icx_plan_tuning")
+        return {"warps_per_cta": t.warps_per_cta, "order": t.order, "l2_prefetch": t.l2_prefetch}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().icx_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ListPool:
+    """Many lists encoded on the GPU into one pooled buffer, one encoder call
+    per list and no host synchronisation until all are issued.
+
+    ``values`` (a host uint32 array) holds the lists back to back, list i at
+    values[offsets[i]:offsets[i+1]]; codecs, deltas, fmts give each list's
+    format.  The values are uploaded with every list starting on a 16-byte
+    boundary (``x``, list i at x[x_off[i]:x_off[i]+n[i]]).  After
+    construction: data (uint8 pool), index (uint64 pool), and per list
+    in_off, in_bytes, index_off (host integers)."""
+
+    def __init__(self, values, offsets, codecs, deltas, fmts=None, device="cuda", stream=None):
+        import numpy as np
+        import torch
+        L = len(offsets) - 1
+        fmts = np.zeros(L, dtype=np.int64) if fmts is None else np.asarray(fmts)
+        self.offsets = np.asarray(offsets, dtype=np.int64)
+        self.n = np.diff(self.offsets)
+        self.codecs, self.deltas, self.fmts = np.asarray(codecs), np.asarray(deltas), fmts
+        padded = (self.n + 3) // 4 * 4
+        self.x_off = np.zeros(L, dtype=np.int64)
+        np.cumsum(padded[:-1], out=self.x_off[1:])
+        host = np.zeros(int(padded.sum()) + 4, dtype=np.uint32)
+        dst = np.repeat(self.x_off - self.offsets[:-1], self.n) + np.arange(int(self.offsets[-1]), dtype=np.int64)
+        host[dst] = np.asarray(values, dtype=np.uint32)[:int(self.offsets[-1])]
+        self.x = torch.from_numpy(host.view(np.int32)).to(device).view(torch.uint32)
+        cap = np.zeros(L, dtype=np.int64)
+        ilen = np.zeros(L, dtype=np.int64)
+        for i in range(L):
+            n = int(self.n[i])
+            if self.codecs[i] == CODEC_BP128:
+                cap[i], ilen[i] = bp128_max_bytes(n, int(fmts[i])), bp128_index_len(n)
+            else:
+                cap[i], ilen[i] = fastpfor_max_bytes(n), fastpfor_index_len(n)
+        cap = (cap + 15) // 16 * 16
+        ilen = (ilen + 1) // 2 * 2
+        self.in_off = np.zeros(L, dtype=np.int64)
+        self.index_off = np.zeros(L, dtype=np.int64)
+        np.cumsum(cap[:-1], out=self.in_off[1:])
+        np.cumsum(ilen[:-1], out=self.index_off[1:])
+        dev = self.x.device
+        self.data = torch.empty(int(cap.sum()) + 16, dtype=torch.uint8, device=dev)
+        self.index = torch.empty(int(ilen.sum()) + 2, dtype=torch.uint64, device=dev)
+        totals = torch.zeros(L, dtype=torch.uint64, device=dev)
+        nmax = int(self.n.max()) if L else 1
+        ews = Workspace(max(nmax, 1), device=dev, stream=stream, encode=True)
+        s = _stream(stream)
+        base_v, base_d, base_i, base_t = self.x.data_ptr(), self.data.data_ptr(), self.index.data_ptr(), \
+            totals.data_ptr()
+        F = lib()
+        for i in range(L):
+            n = int(self.n[i])
+            args = (ctypes.c_void_p(base_v + 4 * int(self.x_off[i])), n)
+            outp = ctypes.c_void_p(base_d + int(self.in_off[i]))
+            idxp = ctypes.c_void_p(base_i + 8 * int(self.index_off[i]))
+            totp = ctypes.c_void_p(base_t + 8 * i)
+            if self.codecs[i] == CODEC_BP128:
+                code = F.bp128_encode(*args, int(self.deltas[i]), int(fmts[i]), outp, int(cap[i]), idxp, totp,
+                                      ews.ptr(), ews.bytes, s)
+            else:
+                code = F.fastpfor_encode(*args, int(self.deltas[i]), outp, int(cap[i]), idxp, totp, ews.ptr(),
+                                         ews.bytes, s)
+            _check(code, f"encode list {i}")
+        ews.raise_status("pooled encode", stream)
+        self.in_bytes = totals.cpu().numpy().view(np.int64).copy()
+        self.cap = cap
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.in_bytes.sum())
+
+    def output_offsets(self):
+        """Per list the first element of its output in a pooled uint32 tensor
+        laid out like ``x`` (16-byte aligned starts), and the pool length."""
+        return self.x_off, int(self.x.numel())
+
+    def descs(self, out, out_off, with_index=True):
+        """ListDesc per list, decoding into out[out_off[i]:out_off[i]+n[i]]."""
+        bd, bi, bo = self.data.data_ptr(), self.index.data_ptr(), out.data_ptr()
+        res = []
+        for i in range(len(self.n)):
+            res.append(ListDesc(bd + int(self.in_off[i]), int(self.in_bytes[i]), bo + 4 * int(out_off[i]),
+                                int(self.n[i]), (bi + 8 * int(self.index_off[i])) if with_index else None,
+                                int(self.codecs[i]), int(self.deltas[i]), int(self.fmts[i])))
+        return res
+

@@ -1,0 +1,882 @@
+// Batched decoding of many independent lists (posting-list-like arrays of
+// uneven length) in one CUDA graph launch.
+//
+// Every list is cut into units exactly as its single-array decoder cuts it:
+// SIMD-BP128 metablocks (2048 integers) or SIMD-FastPFOR units of 16 blocks
+// of a page, then the Variable Byte tail if n % 128 != 0.  The plan lays all
+// units of all lists out in one work-list (lists contiguous, in a tuned
+// order).  One persistent kernel takes tiles of W consecutive work items
+// (dynamic tile ids); per tile each warp decodes one unit exactly like the
+// single-array kernels, and the carries of differential decoding (Sec. 3)
+// come from a segmented scan over the tile plus a decoupled look-back that
+// only ever follows the tile's first list:
+//   * a tile whose first unit starts a list needs no carry-in;
+//   * a tile publishes the running sum of its LAST list: as an inclusive
+//     prefix right away when that list starts inside the tile, else as an
+//     aggregate that becomes an inclusive prefix after its own look-back.
+// So a look-back chain never leaves a list, and short lists never wait.
+// Before it, one page-parse launch covers every SIMD-FastPFOR page of every
+// list (the same parse as the single-array decoder).
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "icx_bp128.cuh"
+#include "icx_fastpfor.cuh"
+#include "icx_kernels.cuh"
+
+namespace icx {
+
+struct __align__(16) ListDev {
+    const uint8_t* in;
+    uint64_t in_bytes;
+    uint32_t* out;
+    uint64_t n;
+    const uint64_t* index;
+    uint32_t page_slot;  // SIMD-FastPFOR: record slot of its first page
+    uint32_t units;      // M: metablocks / 16-block units (the tail is unit M)
+    uint32_t tail_at;    // index entry where the Variable Byte tail starts
+    uint8_t codec, delta, fmt, pad;
+    uint32_t pad2[2];
+};
+static_assert(sizeof(ListDev) == 64, "list record");
+
+constexpr int kBatchHdr = 1024;
+constexpr int kBatchBuf = kBuf > kFBuf ? kBuf : kFBuf;
+// per warp: staging buffer, 16 block records, exception scratch, unit context
+struct WarpCtx {
+    ListDev L;
+    uint64_t pbase;  // SIMD-FastPFOR: byte offset of the unit's page
+    uint32_t u, K, size, slot;
+    uint32_t valid, list, pad[4];
+};
+static_assert(sizeof(WarpCtx) == 112, "warp context");
+constexpr int kWarpBytes = kBatchBuf + 16 * 16 + 2048 + (int)sizeof(WarpCtx);
+static_assert(kWarpBytes % 16 == 0, "warp region");
+
+struct BatchShared {
+    uint4 agg[kMaxWarps];
+    uint4 pref[kMaxWarps];
+    uint32_t list[kMaxWarps];
+    uint32_t start[kMaxWarps];
+    uint32_t nx[2];
+};
+static_assert(sizeof(BatchShared) + 8 * kMaxWarps <= kBatchHdr, "batch header");
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void __launch_bounds__(kMetaThreads)
+    batch_meta_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ pages,
+                      BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
+                      WsHeader* h) {
+    __shared__ MetaSmem S;
+    const uint2 pi = pages[blockIdx.x];  // (list, page); slot = blockIdx.x
+    const ListDev& L = lists[pi.x];
+    const uint64_t nb = L.n / 128;
+    const uint32_t K = (uint32_t)min((uint64_t)kBlocksPerPage, nb - (uint64_t)kBlocksPerPage * pi.y);
+    const size_t g = blockIdx.x;
+    parse_page(S, L.in, L.in_bytes, L.index[pi.y], L.index[pi.y + 1], K, meta + kBlocksPerPage * g,
+               pmeta + kPageMetaWords * g, umeta + kUnitsPerPage * g, h);
+}
+
+// Byte range of every SIMD-BP128 work item (for the L2 prefetch ahead).
+__global__ void batch_ranges_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
+                                    ulonglong2* __restrict__ ranges) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nwork) return;
+    const uint2 wi = work[i];
+    const ListDev& L = lists[wi.x];
+    ulonglong2 r = make_ulonglong2(0, 0);
+    if (L.codec == ICX_CODEC_BP128 && wi.y < L.units) {
+        const uint64_t off = L.index[wi.y], end = L.index[wi.y + 1];
+        if (off <= end && end <= L.in_bytes && end - off <= kMetaMax && ((off | end) & 15) == 0)
+            r = make_ulonglong2(reinterpret_cast<uint64_t>(L.in + off), end - off);
+    }
+    ranges[i] = r;
+}
+
+// Index of a list stored without one (at most one metablock / page): entry 0
+// = 0 and entry 1 = the end of that metablock / page (where the tail starts).
+__global__ void batch_mini_index_kernel(const ListDev* __restrict__ lists, const uint32_t* __restrict__ ids,
+                                        uint32_t count, uint64_t* __restrict__ mini, WsHeader* h) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const ListDev& L = lists[ids[j]];
+    uint64_t* ix = mini + 2 * (size_t)j;
+    const uint64_t nb = L.n / 128;
+    uint64_t end = 0;
+    bool bad = false;
+    if (nb > 0) {
+        if (L.codec == ICX_CODEC_BP128) {
+            if (L.in_bytes < 16) {
+                bad = true;
+            } else {
+                const uint4 d = *reinterpret_cast<const uint4*>(L.in);
+                uint32_t sum = 0;
+                for (uint32_t k = 0; k < nb; ++k) {
+                    const uint32_t b = desc_width(d, (int)k);
+                    bad |= b > 32;
+                    sum += b;
+                }
+                end = L.fmt == ICX_FMT_PAPER ? 16 + 16 * (uint64_t)sum : 16 + 128 * (uint64_t)((4 * sum + 31) / 32);
+            }
+        } else {
+            if (L.in_bytes < 16) {
+                bad = true;
+            } else {
+                const uint64_t len_at = 4 * (uint64_t)ld32(L.in);
+                bad = len_at < 16 || (len_at & 15) || len_at + 4 > L.in_bytes;
+                uint64_t q = 0;
+                if (!bad) {
+                    q = len_at + 4 + pad_up(ld32(L.in + len_at), 4);
+                    bad = q + 4 > L.in_bytes;
+                }
+                if (!bad) {
+                    const uint32_t bitset = ld32(L.in + q);
+                    q += 4;
+                    for (int d = 1; d <= 32 && !bad; ++d) {
+                        if (!((bitset >> (d - 1)) & 1u)) continue;
+                        if (q + 4 > L.in_bytes) {
+                            bad = true;
+                            break;
+                        }
+                        const uint64_t cnt = ld32(L.in + q);
+                        q = pad_up(q + 4, 16) + 16 * (uint64_t)d * ((cnt + 127) / 128);
+                    }
+                }
+                end = pad_up(q, 16);
+            }
+        }
+        if (end > L.in_bytes) bad = true;
+    }
+    ix[0] = 0;
+    ix[1] = bad ? L.in_bytes : end;
+    if (bad) set_error(h, ICX_ECORRUPT);
+}
+
+// One look-back state per chain for `tile`: flag 1 = aggregate, 2 = prefix.
+__device__ __forceinline__ void publish_state(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 v, bool prefix) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t tag = (epoch << 2) | (prefix ? 2u : 1u);
+    if (lane < 4)
+        st_relaxed(tile_states(h) + (size_t)tile * kStatesPerTile + lane,
+                   ((unsigned long long)tag << 32) | comp(v, lane));
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
+    batch_decode_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
+                        const ulonglong2* __restrict__ ranges, const BlockMeta* __restrict__ meta,
+                        const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, bool l2_ahead,
+                        WsHeader* h) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    BatchShared& S = *reinterpret_cast<BatchShared*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kBatchHdr) - kMaxWarps + warp;
+    uint8_t* wbase = smem_raw + kBatchHdr + (size_t)warp * kWarpBytes;
+    uint8_t* buf = wbase;
+    BlockMeta* m = reinterpret_cast<BlockMeta*>(wbase + kBatchBuf);
+    uint8_t* blk_of = wbase + kBatchBuf + 256;
+    WarpCtx& C = *reinterpret_cast<WarpCtx*>(wbase + kBatchBuf + 256 + 2048);
+    const uint32_t ntiles = (nwork + W - 1) / W;
+    const uint32_t epoch = launch_epoch(h);
+    if (lane == 0) mbar_init(bar, 1);
+    fence_mbar_init();
+    if (threadIdx.x == 0) S.nx[0] = atomicAdd(&h->tile_counter, 1u);
+    __syncthreads();
+    uint32_t phase = 0, it = 0;
+    bool broken = false;
+
+    // loads work item i into the warp context and starts its bulk copy;
+    // C.size: bytes in flight (0: none, ~0u: invalid)
+    auto issue = [&](uint32_t i) {
+        __syncwarp();
+        if (i >= nwork) {
+            if (lane == 0) C.valid = 0;
+            __syncwarp();
+            return;
+        }
+        const uint2 wi = work[i];
+        if (lane < 4) reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + wi.x)[lane];
+        __syncwarp();
+        const uint32_t u = wi.y, M = C.L.units;
+        const uint64_t nb = C.L.n / 128;
+        const uint32_t K = u < M ? (uint32_t)min((uint64_t)16, nb - 16 * (uint64_t)u) : 0u;
+        uint32_t size = 0, slot = 0;
+        uint64_t pbase = 0;
+        if (u < M && C.L.codec == ICX_CODEC_FASTPFOR) {
+            const uint32_t p = u / kUnitsPerPage, q = u % kUnitsPerPage;
+            slot = C.L.page_slot + p;
+            if ((uint32_t)lane < K)
+                reinterpret_cast<uint4*>(m)[lane] =
+                    reinterpret_cast<const uint4*>(meta + (size_t)kBlocksPerPage * slot + 16 * q)[lane];
+            if (lane == 0) {
+                const uint2 um = umeta[(size_t)kUnitsPerPage * slot + q];
+                const bool bad = pmeta[(size_t)kPageMetaWords * slot + 32] != 0;
+                pbase = C.L.index[p];
+                size = bad ? ~0u : um.y;
+                if (!broken && !bad && um.y) {
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, um.y);
+                    bulk_load(buf, C.L.in + pbase + um.x, um.y, bar);
+                }
+            }
+        } else if (u < M && lane == 0) {
+            const uint64_t off = C.L.index[u], end = C.L.index[u + 1];
+            const bool ok = off <= end && end <= C.L.in_bytes && end - off >= 16 && end - off <= kMetaMax &&
+                            ((off | end) & 15) == 0;
+            size = ok ? (uint32_t)(end - off) : ~0u;
+            if (ok && !broken) {
+                fence_proxy_async();
+                mbar_expect_tx(bar, size);
+                bulk_load(buf, C.L.in + off, size, bar);
+            }
+        }
+        if (lane == 0) {
+            C.list = wi.x;
+            C.u = u;
+            C.K = K;
+            C.size = size;
+            C.slot = slot;
+            C.pbase = pbase;
+            C.valid = 1;
+        }
+        __syncwarp();
+    };
+
+    uint32_t tile = S.nx[0];
+    if (tile < ntiles) issue(tile * W + warp);
+
+    while (tile < ntiles) {
+        const uint32_t i = tile * W + warp;
+        uint4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
+        const bool valid = C.valid != 0;
+        const uint32_t u = C.u, K = C.K, size = C.size, M = C.L.units;
+        const int codec = C.L.codec, delta = C.L.delta, fmt = C.L.fmt;
+        uint32_t Ks = 0;  // blocks to scan and store
+        bool residue = false;
+        ulonglong2 pf = make_ulonglong2(0, 0);
+        if (l2_ahead && lane == 0 && i + gridDim.x * W < nwork) pf = ranges[i + gridDim.x * W];
+        if (valid && u < M) {
+            Ks = K;
+            bool ok = size != ~0u && !broken;
+            if (size == ~0u) {
+                if (lane == 0) set_error(h, ICX_ECORRUPT);
+            } else if (ok && size != 0) {
+                ok = __all_sync(FULL, mbar_wait(bar, phase));
+                phase ^= 1;
+                if (!ok) {
+                    broken = true;
+                    if (lane == 0) set_error(h, ICX_ETIMEOUT);
+                }
+            }
+            if (lane == 0 && pf.y) prefetch_l2(reinterpret_cast<const void*>(pf.x), (uint32_t)pf.y);
+            if (ok) {
+                if (codec == ICX_CODEC_FASTPFOR) {
+                    fp_unit_unpack_patch(C.L.in, C.pbase, pmeta + (size_t)kPageMetaWords * C.slot, m, K, buf, blk_of,
+                                         v, h, lane);
+                } else if (fmt == ICX_FMT_W32) {
+                    ok = bp128_unpack_unit<ICX_FMT_W32>(buf, size, K, v, h, lane);
+                    residue = ok;
+                } else {
+                    bp128_unpack_unit<ICX_FMT_PAPER>(buf, size, K, v, h, lane);
+                }
+            }
+            __syncwarp();
+        } else if (valid) {
+            const uint32_t count = (uint32_t)(C.L.n % 128);
+            if (count) {
+                tail_unit(C.L.in, C.L.in_bytes, C.L.index[C.L.tail_at], count, reinterpret_cast<uint32_t*>(buf), v,
+                          h, lane);
+                Ks = 1;
+            }
+        }
+        // unit aggregate straight after unpacking
+        uint4 agg = make_uint4(0, 0, 0, 0);
+        if (valid && delta == ICX_DELTA_1) agg = unit_sum<ICX_DELTA_1>(v, residue);
+        if (valid && delta == ICX_DELTA_4) agg = unit_sum<ICX_DELTA_4>(v, residue);
+        if (lane == 0) {
+            S.agg[warp] = agg;
+            S.list[warp] = valid ? C.list : 0xFFFFFFFFu - (uint32_t)warp;
+            S.start[warp] = valid && u == 0;
+        }
+        __syncthreads();
+        // warp 0: segmented scan of the tile (segments = lists), publish the
+        // last list's running sum, look back for the first list if needed
+        uint4 a = make_uint4(0, 0, 0, 0), incl = a;
+        uint32_t first_b = W;
+        bool need_carry = false, single = true;
+        if (warp == 0) {
+            const bool have = lane < W;
+            a = have ? S.agg[lane] : make_uint4(0, 0, 0, 0);
+            const uint32_t li = have ? S.list[lane] : 0xFFFFFFF0u - (uint32_t)lane;
+            const uint32_t lp = __shfl_up_sync(FULL, li, 1);
+            const bool bnd = lane == 0 || li != lp;
+            incl = a;
+            bool f = bnd;
+#pragma unroll
+            for (int off = 1; off < W; off <<= 1) {
+                const uint4 y = make_uint4(__shfl_up_sync(FULL, incl.x, off), __shfl_up_sync(FULL, incl.y, off),
+                                           __shfl_up_sync(FULL, incl.z, off), __shfl_up_sync(FULL, incl.w, off));
+                const bool fy = __shfl_up_sync(FULL, f, off);
+                if (lane >= off) {
+                    if (!f) incl = add4(incl, y);
+                    f = f || fy;
+                }
+            }
+            const unsigned bm = __ballot_sync(FULL, bnd && lane > 0 && lane < W);
+            first_b = bm ? (uint32_t)(__ffs(bm) - 1) : (uint32_t)W;
+            single = bm == 0;
+            need_carry = S.start[0] == 0;
+            const uint4 last = shfl4(incl, W - 1);
+            // the last list's running sum: a prefix unless it is the tile's
+            // first list and that list started in an earlier tile
+            publish_state(h, epoch, tile, last, !(single && need_carry));
+        }
+        if (valid && delta == ICX_DELTA_1) {
+            unit_local_scan<ICX_DELTA_1>(v, Ks, residue, lane);
+        } else if (valid && delta == ICX_DELTA_4) {
+            if (residue)
+                unit_local_scan<ICX_DELTA_4>(v, Ks, true, lane);
+            else
+                unit_scan_d4_smem(v, reinterpret_cast<uint32_t*>(buf), lane);
+        } else if (residue) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = residue_to_row(v[k], lane);
+        }
+        if (warp == 0) {
+            uint4 carry = make_uint4(0, 0, 0, 0);
+            if (need_carry) carry = lookback_resolve<4>(h, epoch, tile, shfl4(incl, W - 1), single);
+            if (lane < W) {
+                uint4 pr = sub4(incl, a);
+                if ((uint32_t)lane < first_b) pr = add4(pr, carry);
+                S.pref[lane] = pr;
+            }
+        }
+        ++it;
+        if (threadIdx.x == 0) S.nx[it & 1] = atomicAdd(&h->tile_counter, 1u);
+        __syncthreads();
+        uint4 pref = S.pref[warp];
+        if (delta == ICX_DELTA_1) pref = make_uint4(pref.x, pref.x, pref.x, pref.x);
+        if (delta == ICX_DELTA_NONE) pref = make_uint4(0, 0, 0, 0);
+        uint32_t* out = C.L.out;
+        const uint64_t n = C.L.n, first = u < M ? 2048 * (uint64_t)u : 128 * (n / 128);
+        const uint32_t next = S.nx[it & 1];
+        // (the context is reloaded by issue(); keep what the stores need)
+        issue(next < ntiles ? next * W + warp : nwork);
+        if (valid && Ks) store_unit(out, first, n, v, Ks, pref, lane);
+        tile = next;
+    }
+    if (broken) mbar_wait(bar, phase);
+    finish_launch(h, epoch);
+}
+
+// ------------------------------------------------------------------ plan
+
+struct PlanMem {
+    ListDev* lists = nullptr;
+    uint2* work = nullptr;
+    ulonglong2* ranges = nullptr;
+    uint2* pages = nullptr;
+    BlockMeta* meta = nullptr;
+    uint32_t* pmeta = nullptr;
+    uint2* umeta = nullptr;
+    uint64_t* mini = nullptr;
+    uint32_t* mini_ids = nullptr;
+    WsHeader* ws = nullptr;
+};
+
+static cudaError_t batch_occupancy(int W, int* blocks, int* sms) {
+    const int smem = kBatchHdr + W * kWarpBytes;
+    cudaError_t e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    if (W == 4) {
+        e = cudaFuncSetAttribute(batch_decode_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<4>, W * 32, smem);
+    } else {
+        e = cudaFuncSetAttribute(batch_decode_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<8>, W * 32, smem);
+    }
+    if (*blocks < 1) *blocks = 1;
+    return e;
+}
+
+}  // namespace icx
+
+using icx::ListDev;
+
+struct icx_plan {
+    int device = 0;
+    std::vector<icx_list_desc> lists;
+    std::vector<ListDev> host_lists;
+    std::vector<uint32_t> items_per_list;  // work items of each list
+    size_t nwork = 0, npages = 0, nmini = 0;
+    size_t max_n = 0;
+    void* mem = nullptr;
+    icx::PlanMem d;
+    icx_tuning tune{8, 0, 1, nullptr};
+    cudaStream_t cap = nullptr;  // capture stream
+    cudaGraphExec_t exec = nullptr;
+    // per-list baseline
+    void* single_ws = nullptr;
+    size_t single_ws_bytes = 0;
+    cudaGraphExec_t per_list_exec = nullptr;
+};
+
+namespace {
+
+thread_local long long g_error_list = -1;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+icx_status check_list(const icx_list_desc& l) {
+    if (!(l.codec == ICX_CODEC_BP128 || l.codec == ICX_CODEC_FASTPFOR)) return ICX_EINVAL;
+    if (!(l.delta == ICX_DELTA_NONE || l.delta == ICX_DELTA_1 || l.delta == ICX_DELTA_4)) return ICX_EINVAL;
+    if (l.codec == ICX_CODEC_BP128 && !(l.fmt == ICX_FMT_PAPER || l.fmt == ICX_FMT_W32)) return ICX_EINVAL;
+    if (l.n == 0) return ICX_OK;
+    if (!l.d_in || !l.d_out) return ICX_EINVAL;
+    if (!aligned16(l.d_in) || !aligned16(l.d_out) || (l.d_index && !aligned16(l.d_index))) return ICX_EALIGN;
+    if (l.n > ((size_t)1 << 36)) return ICX_EINVAL;
+    const size_t nb = l.n / 128;
+    if (!l.d_index) {
+        const bool small = l.codec == ICX_CODEC_BP128 ? (nb + 15) / 16 <= 1 : (nb + 511) / 512 <= 1;
+        if (!small) return ICX_EINVAL;
+    }
+    return ICX_OK;
+}
+
+// work-list: lists contiguous, in the tuned order
+std::vector<uint2> build_work(const icx_plan& p, int order) {
+    const size_t L = p.lists.size();
+    std::vector<uint32_t> ids(L);
+    for (size_t i = 0; i < L; ++i) ids[i] = (uint32_t)i;
+    if (order == 1)
+        std::stable_sort(ids.begin(), ids.end(),
+                         [&](uint32_t a, uint32_t b) { return p.items_per_list[a] > p.items_per_list[b]; });
+    else if (order == 2)
+        std::stable_sort(ids.begin(), ids.end(),
+                         [&](uint32_t a, uint32_t b) { return p.items_per_list[a] < p.items_per_list[b]; });
+    std::vector<uint2> w;
+    w.reserve(p.nwork);
+    for (uint32_t id : ids)
+        for (uint32_t u = 0; u < p.items_per_list[id]; ++u) w.push_back(make_uint2(id, u));
+    return w;
+}
+
+cudaError_t capture(icx_plan* p) {
+    using namespace icx;
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    const int W = p->tune.warps_per_cta;
+    const int smem = kBatchHdr + W * kWarpBytes;
+    int blocks = 1, sms = 1;
+    cudaError_t e = batch_occupancy(W, &blocks, &sms);
+    if (e != cudaSuccess) return e;
+    const size_t ntiles = (p->nwork + W - 1) / W;
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)blocks * sms, ntiles));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    if (p->npages)
+        batch_meta_kernel<<<(unsigned)p->npages, kMetaThreads, 0, p->cap>>>(p->d.lists, p->d.pages, p->d.meta,
+                                                                           p->d.pmeta, p->d.umeta, p->d.ws);
+    if (p->nwork) {
+        if (W == 4)
+            batch_decode_kernel<4><<<grid, 4 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
+                                                                   p->d.ranges, p->d.meta, p->d.pmeta, p->d.umeta,
+                                                                   p->tune.l2_prefetch != 0, p->d.ws);
+        else
+            batch_decode_kernel<8><<<grid, 8 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
+                                                                   p->d.ranges, p->d.meta, p->d.pmeta, p->d.umeta,
+                                                                   p->tune.l2_prefetch != 0, p->d.ws);
+    }
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(p->cap, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+cudaError_t apply_order(icx_plan* p, int order) {
+    const std::vector<uint2> w = build_work(*p, order);
+    if (w.empty()) return cudaSuccess;
+    cudaError_t e = cudaMemcpy(p->d.work, w.data(), w.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    icx::batch_ranges_kernel<<<(unsigned)((w.size() + 255) / 256), 256, 0, p->cap>>>(p->d.lists, p->d.work,
+                                                                                    (uint32_t)w.size(), p->d.ranges);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->cap);
+    return e;
+}
+
+// ------------------------------------------------------------ tuning cache
+
+std::string signature(const icx_plan& p) {
+    uint64_t hsh = 1469598103934665603ull;  // FNV-1a over (n, codec, delta, fmt)
+    auto mix = [&](uint64_t x) {
+        for (int b = 0; b < 8; ++b) {
+            hsh ^= (x >> (8 * b)) & 0xFF;
+            hsh *= 1099511628211ull;
+        }
+    };
+    for (const auto& l : p.lists) {
+        mix(l.n);
+        mix((uint64_t)l.codec | (uint64_t)l.delta << 8 | (uint64_t)l.fmt << 16);
+    }
+    char buf[96];
+    snprintf(buf, sizeof buf, "lists=%zu;units=%zu;h=%016llx", p.lists.size(), p.nwork, (unsigned long long)hsh);
+    return buf;
+}
+
+const char* cache_file(const icx_tuning* t) {
+    if (t && t->cache_path) return t->cache_path;
+    return std::getenv("ICX_TUNE_CACHE");
+}
+
+// The cache is a flat JSON object {"<signature>": [W, order, l2], ...}.
+bool cache_lookup(const char* path, const std::string& key, int* W, int* order, int* l2) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return false;
+    std::string s;
+    char chunk[4096];
+    size_t r;
+    while ((r = std::fread(chunk, 1, sizeof chunk, f)) > 0) s.append(chunk, r);
+    std::fclose(f);
+    const std::string k = "\"" + key + "\"";
+    const size_t at = s.find(k);
+    if (at == std::string::npos) return false;
+    const size_t lb = s.find('[', at + k.size());
+    if (lb == std::string::npos) return false;
+    return std::sscanf(s.c_str() + lb, "[%d, %d, %d]", W, order, l2) == 3 && (*W == 4 || *W == 8) && *order >= 0 &&
+           *order <= 2 && (*l2 == 0 || *l2 == 1);
+}
+
+void cache_store(const char* path, const std::string& key, int W, int order, int l2) {
+    if (!path) return;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    std::vector<std::pair<std::string, std::string>> entries;
+    if (FILE* f = std::fopen(path, "rb")) {
+        std::string s;
+        char chunk[4096];
+        size_t r;
+        while ((r = std::fread(chunk, 1, sizeof chunk, f)) > 0) s.append(chunk, r);
+        std::fclose(f);
+        size_t pos = 0;
+        for (;;) {
+            const size_t q0 = s.find('"', pos);
+            if (q0 == std::string::npos) break;
+            const size_t q1 = s.find('"', q0 + 1);
+            const size_t lb = s.find('[', q1);
+            const size_t rb = s.find(']', lb);
+            if (q1 == std::string::npos || lb == std::string::npos || rb == std::string::npos) break;
+            entries.emplace_back(s.substr(q0 + 1, q1 - q0 - 1), s.substr(lb, rb - lb + 1));
+            pos = rb + 1;
+        }
+    }
+    char val[64];
+    snprintf(val, sizeof val, "[%d, %d, %d]", W, order, l2);
+    bool found = false;
+    for (auto& e : entries)
+        if (e.first == key) {
+            e.second = val;
+            found = true;
+        }
+    if (!found) entries.emplace_back(key, val);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    std::fputs("{\n", f);
+    for (size_t i = 0; i < entries.size(); ++i)
+        std::fprintf(f, "  \"%s\": %s%s\n", entries[i].first.c_str(), entries[i].second.c_str(),
+                     i + 1 < entries.size() ? "," : "");
+    std::fputs("}\n", f);
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+cudaError_t time_config(icx_plan* p, float* ms) {
+    cudaError_t e = capture(p);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    e = cudaGraphLaunch(p->exec, p->cap);  // warm-up
+    std::vector<float> t;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+        cudaEventRecord(a, p->cap);
+        e = cudaGraphLaunch(p->exec, p->cap);
+        cudaEventRecord(b, p->cap);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float x = 0;
+        cudaEventElapsedTime(&x, a, b);
+        t.push_back(x);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return e;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long icx_plan_error_list(void) { return g_error_list; }
+
+icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_tuning* t, icx_plan** out) {
+    using namespace icx;
+    g_error_list = -1;
+    if (!out || (!lists && nlists)) return ICX_EINVAL;
+    *out = nullptr;
+    if (nlists >= 0x80000000u) return ICX_EINVAL;
+    if (t && ((t->warps_per_cta != 0 && t->warps_per_cta != 4 && t->warps_per_cta != 8) || t->order < -1 ||
+              t->order > 2 || t->l2_prefetch < -1 || t->l2_prefetch > 1))
+        return ICX_EINVAL;
+    for (size_t i = 0; i < nlists; ++i) {
+        const icx_status st = check_list(lists[i]);
+        if (st != ICX_OK) {
+            g_error_list = (long long)i;
+            return st;
+        }
+    }
+    icx_plan* p = new icx_plan();
+    cudaGetDevice(&p->device);
+    p->lists.assign(lists, lists + nlists);
+    p->host_lists.resize(nlists);
+    p->items_per_list.resize(nlists);
+    std::vector<uint2> pages;
+    std::vector<uint32_t> mini_ids;
+    for (size_t i = 0; i < nlists; ++i) {
+        const icx_list_desc& l = lists[i];
+        ListDev& d = p->host_lists[i];
+        std::memset(&d, 0, sizeof d);
+        const size_t nb = l.n / 128, M = (nb + 15) / 16;
+        d.in = l.d_in;
+        d.in_bytes = l.d_in ? l.in_bytes : 0;
+        d.out = l.d_out;
+        d.n = l.n;
+        d.index = l.d_index;
+        d.units = (uint32_t)M;
+        d.codec = (uint8_t)l.codec;
+        d.delta = (uint8_t)l.delta;
+        d.fmt = (uint8_t)(l.codec == ICX_CODEC_BP128 ? l.fmt : 0);
+        if (l.codec == ICX_CODEC_FASTPFOR) {
+            const size_t P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
+            d.page_slot = (uint32_t)pages.size();
+            d.tail_at = (uint32_t)P;
+            for (size_t q = 0; q < P; ++q) pages.push_back(make_uint2((uint32_t)i, (uint32_t)q));
+        } else {
+            d.tail_at = (uint32_t)M;
+        }
+        if (l.n && !l.d_index) mini_ids.push_back((uint32_t)i);
+        p->items_per_list[i] = l.n ? (uint32_t)(M + (l.n % 128 ? 1 : 0)) : 0u;
+        p->nwork += p->items_per_list[i];
+        p->max_n = std::max(p->max_n, l.n);
+    }
+    p->npages = pages.size();
+    p->nmini = mini_ids.size();
+    if (p->nwork > 0xFFFFFFF0ull / 2) {
+        delete p;
+        return ICX_EINVAL;
+    }
+    // one allocation for everything
+    const size_t ntiles_max = (p->nwork + 3) / 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return at;
+    };
+    const size_t o_lists = take(sizeof(ListDev) * nlists), o_work = take(sizeof(uint2) * p->nwork),
+                 o_ranges = take(sizeof(ulonglong2) * p->nwork), o_pages = take(sizeof(uint2) * p->npages),
+                 o_meta = take(sizeof(BlockMeta) * kBlocksPerPage * p->npages),
+                 o_pmeta = take(4 * kPageMetaWords * p->npages), o_umeta = take(8 * kUnitsPerPage * p->npages),
+                 o_mini = take(16 * p->nmini), o_ids = take(4 * p->nmini),
+                 o_ws = take(kWsHeaderBytes + 32 * (ntiles_max + 16));
+    if (cudaMalloc(&p->mem, off) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return ICX_ENOSPC;
+    }
+    char* base = static_cast<char*>(p->mem);
+    p->d.lists = reinterpret_cast<ListDev*>(base + o_lists);
+    p->d.work = reinterpret_cast<uint2*>(base + o_work);
+    p->d.ranges = reinterpret_cast<ulonglong2*>(base + o_ranges);
+    p->d.pages = reinterpret_cast<uint2*>(base + o_pages);
+    p->d.meta = reinterpret_cast<BlockMeta*>(base + o_meta);
+    p->d.pmeta = reinterpret_cast<uint32_t*>(base + o_pmeta);
+    p->d.umeta = reinterpret_cast<uint2*>(base + o_umeta);
+    p->d.mini = reinterpret_cast<uint64_t*>(base + o_mini);
+    p->d.mini_ids = reinterpret_cast<uint32_t*>(base + o_ids);
+    p->d.ws = reinterpret_cast<WsHeader*>(base + o_ws);
+    for (size_t j = 0; j < p->nmini; ++j) p->host_lists[mini_ids[j]].index = p->d.mini + 2 * j;
+    auto fail = [&](icx_status st) {
+        icx_plan_destroy(p);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(ICX_ECUDA);
+    if (nlists &&
+        cudaMemcpy(p->d.lists, p->host_lists.data(), sizeof(ListDev) * nlists, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ICX_ECUDA);
+    if (p->npages &&
+        cudaMemcpy(p->d.pages, pages.data(), sizeof(uint2) * p->npages, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ICX_ECUDA);
+    if (cudaMemset(p->d.ws, 0, kWsHeaderBytes + 32 * (ntiles_max + 16)) != cudaSuccess) return fail(ICX_ECUDA);
+    if (p->nmini) {
+        if (cudaMemcpy(p->d.mini_ids, mini_ids.data(), 4 * p->nmini, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(ICX_ECUDA);
+        batch_mini_index_kernel<<<(unsigned)((p->nmini + 127) / 128), 128, 0, p->cap>>>(
+            p->d.lists, p->d.mini_ids, (uint32_t)p->nmini, p->d.mini, p->d.ws);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->cap) != cudaSuccess) return fail(ICX_ECUDA);
+    }
+    // tuning: explicit fields, then the cache, then timing
+    int W = t ? t->warps_per_cta : 0, order = t ? t->order : -1, l2 = t ? t->l2_prefetch : -1;
+    if (!t) {
+        W = 0;
+        order = -1;
+        l2 = -1;
+    }
+    p->tune.cache_path = nullptr;
+    if (W == 0 || order < 0 || l2 < 0) {
+        const std::string key = signature(*p);
+        const char* path = cache_file(t);
+        int cW, cO, cL;
+        if (cache_lookup(path, key, &cW, &cO, &cL)) {
+            if (W == 0) W = cW;
+            if (order < 0) order = cO;
+            if (l2 < 0) l2 = cL;
+        } else {
+            float best = 3.4e38f;
+            int bW = 8, bO = 0, bL = 1;
+            for (int w : {4, 8}) {
+                if (W && w != W) continue;
+                for (int o = 0; o <= 2; ++o) {
+                    if (order >= 0 && o != order) continue;
+                    if (apply_order(p, o) != cudaSuccess) return fail(ICX_ECUDA);
+                    for (int q = 0; q <= 1; ++q) {
+                        if (l2 >= 0 && q != l2) continue;
+                        p->tune.warps_per_cta = w;
+                        p->tune.order = o;
+                        p->tune.l2_prefetch = q;
+                        float ms = 0;
+                        if (time_config(p, &ms) != cudaSuccess) return fail(ICX_ECUDA);
+                        if (ms < best) {
+                            best = ms;
+                            bW = w;
+                            bO = o;
+                            bL = q;
+                        }
+                    }
+                }
+            }
+            W = bW;
+            order = bO;
+            l2 = bL;
+            cache_store(path, key, W, order, l2);
+        }
+    }
+    p->tune.warps_per_cta = W;
+    p->tune.order = order;
+    p->tune.l2_prefetch = l2;
+    if (apply_order(p, order) != cudaSuccess) return fail(ICX_ECUDA);
+    if (capture(p) != cudaSuccess) return fail(ICX_ECUDA);
+    *out = p;
+    return ICX_OK;
+}
+
+icx_status icx_plan_launch(icx_plan* p, icx_stream_t stream) {
+    if (!p) return ICX_EINVAL;
+    if (!p->nwork && !p->npages) return ICX_OK;
+    return cudaGraphLaunch(p->exec, (cudaStream_t)stream) == cudaSuccess ? ICX_OK : ICX_ECUDA;
+}
+
+icx_status icx_plan_launch_per_list(icx_plan* p, icx_stream_t stream) {
+    using namespace icx;
+    if (!p) return ICX_EINVAL;
+    if (!p->per_list_exec) {
+        p->single_ws_bytes = ws_total_bytes(std::max<size_t>(p->max_n, 1));
+        if (!p->single_ws) {
+            if (cudaMalloc(&p->single_ws, p->single_ws_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return ICX_ENOSPC;
+            }
+            if (cudaMemset(p->single_ws, 0, p->single_ws_bytes) != cudaSuccess) return ICX_ECUDA;
+        }
+        WsHeader* h = static_cast<WsHeader*>(p->single_ws);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ICX_ECUDA;
+        cudaError_t le = cudaSuccess;
+        for (size_t i = 0; i < p->lists.size() && le == cudaSuccess; ++i) {
+            const icx_list_desc& l = p->lists[i];
+            if (!l.n) continue;
+            const uint64_t* index = p->host_lists[i].index;
+            if (l.codec == ICX_CODEC_BP128)
+                le = launch_bp128_decode(l.delta, l.fmt, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
+            else
+                le = launch_fastpfor_decode(l.delta, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
+        }
+        cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->per_list_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return ICX_ECUDA;
+    }
+    return cudaGraphLaunch(p->per_list_exec, (cudaStream_t)stream) == cudaSuccess ? ICX_OK : ICX_ECUDA;
+}
+
+icx_status icx_plan_status(icx_plan* p, icx_stream_t stream, icx_status* out) {
+    using namespace icx;
+    if (!p || !out) return ICX_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return ICX_ECUDA;
+    unsigned a = 0, b = 0;
+    const size_t at = offsetof(WsHeader, status);
+    if (cudaMemcpy(&a, reinterpret_cast<char*>(p->d.ws) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ICX_ECUDA;
+    if (p->single_ws &&
+        cudaMemcpy(&b, static_cast<char*>(p->single_ws) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ICX_ECUDA;
+    cudaMemset(reinterpret_cast<char*>(p->d.ws) + at, 0, 4);
+    if (p->single_ws) cudaMemset(static_cast<char*>(p->single_ws) + at, 0, 4);
+    if (cudaDeviceSynchronize() != cudaSuccess) return ICX_ECUDA;
+    *out = (icx_status)(a ? a : b);
+    return ICX_OK;
+}
+
+icx_status icx_plan_tuning(const icx_plan* p, icx_tuning* out) {
+    if (!p || !out) return ICX_EINVAL;
+    *out = p->tune;
+    return ICX_OK;
+}
+
+void icx_plan_destroy(icx_plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->per_list_exec) cudaGraphExecDestroy(p->per_list_exec);
+    if (p->cap) {
+        cudaStreamSynchronize(p->cap);
+        cudaStreamDestroy(p->cap);
+    }
+    if (p->mem) cudaFree(p->mem);
+    if (p->single_ws) cudaFree(p->single_ws);
+    delete p;
+}
+
+}  // extern "C"

@@ -8,45 +8,15 @@
 // blocks into registers (64 integers per lane), scans them locally, and the
 // CTA obtains its carry-in with one decoupled look-back per tile before the
 // 128-bit stores.  Every wait is bounded (see icx_device.cuh).
+#include "icx_bp128.cuh"
 #include "icx_kernels.cuh"
-#include "icx_tile.cuh"
 
 namespace icx {
 
 // ---------------------------------------------------------------- decode
 
-constexpr int kMetaMax = 16 + 16 * 16 * 32;  // 8208: every width 32
-constexpr int kPipeHdr = 1024;                // TileShared, then two mbarriers per warp
+constexpr int kPipeHdr = 1024;  // TileShared, then two mbarriers per warp
 static_assert(sizeof(TileShared) + 16 * kMaxWarps <= kPipeHdr, "tile header");
-constexpr int kBuf = kMetaMax + 128;         // slack for reading one row past
-
-
-template <int FMT>
-__device__ __forceinline__ uint4 unpack_block(const uint8_t* buf, uint32_t base_bytes, uint32_t bitbase,
-                                              uint32_t b, int lane) {
-    const uint32_t mask = width_mask(b);
-    if (FMT == ICX_FMT_PAPER) {
-        // Fig. 7 generalised: lane t extracts field t of each of the 4 lanes
-        // (integers 4t..4t+3) from rows (t*b)/32 and the next one.
-        const uint32_t bit = (uint32_t)lane * b;
-        const uint4* rows = reinterpret_cast<const uint4*>(buf + base_bytes);
-        const uint4 r0 = rows[bit >> 5], r1 = rows[(bit >> 5) + 1];
-        const uint32_t s = bit & 31;
-        return make_uint4(__funnelshift_r(r0.x, r1.x, s) & mask, __funnelshift_r(r0.y, r1.y, s) & mask,
-                          __funnelshift_r(r0.z, r1.z, s) & mask, __funnelshift_r(r0.w, r1.w, s) & mask);
-    } else {
-        // W32: lane j's own column; fields m = 0..3 at bits bitbase + m*b.
-        const uint32_t* col = reinterpret_cast<const uint32_t*>(buf + 16) + lane;
-        uint32_t r[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const uint32_t bit = bitbase + (uint32_t)m * b;
-            const uint32_t w = bit >> 5;
-            r[m] = __funnelshift_r(col[32 * w], col[32 * (w + 1)], bit & 31) & mask;
-        }
-        return make_uint4(r[0], r[1], r[2], r[3]);
-    }
-}
 
 // A CTA of W warps takes tiles of W consecutive units (unit u < M is
 // metablock u, unit M the Variable Byte tail); tile ids come from the
@@ -131,32 +101,8 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
                 ((pf_off | pf_end) & 15) == 0)
                 prefetch_l2(in + pf_off, (uint32_t)(pf_end - pf_off));
             if (ok) {
-                const uint4 desc = *reinterpret_cast<const uint4*>(buf);
-                uint32_t sum = 0, maxw = 0;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const uint32_t b = ((uint32_t)k < K) ? (comp(desc, k >> 2) >> (8 * (k & 3))) & 255u : 0u;
-                    sum += b;
-                    maxw = max(maxw, b);
-                }
-                const uint32_t want = FMT == ICX_FMT_PAPER ? 16 + 16 * sum : 16 + 128 * ((4 * sum + 31) / 32);
-                if (maxw > 32 || want != size) {
-                    ok = false;
-                    if (lane == 0) set_error(h, ICX_ECORRUPT);
-                }
-                if (ok) {
-                    uint32_t base = 16, bitbase = 0;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        if ((uint32_t)k < K) {
-                            const uint32_t b = (comp(desc, k >> 2) >> (8 * (k & 3))) & 255u;
-                            v[k] = unpack_block<FMT>(buf, base, bitbase, b, lane);
-                            base += 16 * b;
-                            bitbase += 4 * b;
-                        }
-                    }
-                    residue = FMT == ICX_FMT_W32;
-                }
+                ok = bp128_unpack_unit<FMT>(buf, size, K, v, h, lane);
+                residue = ok && FMT == ICX_FMT_W32;
             }
             __syncwarp();
         } else if (u == M) {

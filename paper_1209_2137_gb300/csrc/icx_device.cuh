@@ -298,10 +298,10 @@ __device__ __forceinline__ void lookback_publish(WsHeader* h, uint32_t epoch, ui
 }
 
 // Resolves the exclusive prefix of `tile` (whose aggregate `agg` is already
-// published) from its predecessors' states and publishes its inclusive
-// prefix.  Whole warp.
+// published) from its predecessors' states and, if `publish`, publishes its
+// inclusive prefix.  Whole warp.
 template <int NL, int R = 4>
-__device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
+__device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg, bool publish = true) {
     static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
     unsigned long long* st = tile_states(h);
@@ -374,7 +374,7 @@ __device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, ui
             acc.w += __shfl_xor_sync(FULL, acc.w, off);
         }
     }
-    if (lane < NL)
+    if (publish && lane < NL)
         st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
                    ((unsigned long long)tagP << 32) | (comp(acc, lane) + comp(agg, lane)));
     return acc;

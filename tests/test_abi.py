@@ -63,3 +63,27 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(icx, "_lib", None)
     with pytest.raises(icx.IcxError):
         icx.lib()
+
+
+def test_plan_create_rejects_bad_lists(lib):
+    # argument checks run on the host before any device call
+    import paper_1209_2137_gb300 as icx
+    tune = {"warps_per_cta": 8, "order": 0, "l2_prefetch": 0}
+    empty = icx.ListDesc(None, 0, None, 0, None, icx.CODEC_BP128, icx.DELTA_1, icx.FMT_PAPER)
+    cases = [
+        (icx.ListDesc(16, 64, 32, 128, 48, 7, 1, 0), icx.EINVAL),            # unknown codec
+        (icx.ListDesc(16, 64, 32, 128, 48, icx.CODEC_BP128, 2, 0), icx.EINVAL),   # stride 2
+        (icx.ListDesc(16, 64, 32, 128, 48, icx.CODEC_BP128, 1, 5), icx.EINVAL),   # layout
+        (icx.ListDesc(20, 64, 32, 128, 48, icx.CODEC_BP128, 1, 0), icx.EALIGN),   # stream not 16-byte aligned
+        (icx.ListDesc(16, 64, 36, 128, 48, icx.CODEC_FASTPFOR, 1, 0), icx.EALIGN),  # output
+        (icx.ListDesc(16, 64, 32, 5000, None, icx.CODEC_BP128, 1, 0), icx.EINVAL),  # 3 metablocks, no index
+        (icx.ListDesc(16, 64, 32, 70000, None, icx.CODEC_FASTPFOR, 1, 0), icx.EINVAL),  # 2 pages, no index
+        (icx.ListDesc(None, 64, 32, 128, 48, icx.CODEC_BP128, 1, 0), icx.EINVAL),  # no stream
+    ]
+    for desc, code in cases:
+        with pytest.raises(icx.IcxError) as e:
+            icx.Plan([empty, empty, desc], tune)
+        assert e.value.code == code and "(list 2)" in str(e.value), (desc.codec, str(e.value))
+    with pytest.raises(icx.IcxError) as e:
+        icx.Plan([empty], {"warps_per_cta": 6, "order": 0, "l2_prefetch": 0})
+    assert e.value.code == icx.EINVAL
