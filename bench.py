@@ -305,6 +305,11 @@ def run_gpu(args, world, rank, local):
     headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
 
     e2e = run_e2e(args, streams, out, ws, dev, world)
+    batched = None
+    if not args.skip_batch:
+        del out
+        torch.cuda.empty_cache()
+        batched = run_batched(args, dev, flush_l2, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(arrays, args)
@@ -323,6 +328,7 @@ def run_gpu(args, world, rank, local):
         "roofline": roofline,
         "headline_kernel": kern[headline],
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": launches_per_step * K,
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -385,6 +391,84 @@ def run_e2e(args, streams, out, ws, dev, world):
     ints = sum(s["n"] for s in streams) * steps * world
     return {"value": round(ints / (ms / 1e3) / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+# ------------------------------------------------------- batched decode --
+
+def run_batched(args, dev, flush_l2, world):
+    """Posting-list batch: Zipf(1.1) list lengths over [128, 2^22] scaled to
+    about 2^28 integers in total (reading A), SIMD-BP128* or SIMD-FastPFOR
+    per list; one graph launch of the plan (tuned on this batch) against one
+    single-array call per list (the same kernels, captured in one graph)."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+    from paper_1209_2137_gb300 import workloads as W
+
+    t0 = time.time()
+    L, offsets, values, bp = W.posting_lists(nlists=args.batch_lists, total=args.batch_total)
+    codecs = np.where(bp, icx.CODEC_BP128, icx.CODEC_FASTPFOR)
+    deltas = np.where(bp, icx.DELTA_4, icx.DELTA_1)
+    pool = icx.ListPool(values, offsets, codecs, deltas, device=dev)
+    del values
+    out_off, total = pool.output_offsets()
+    out = torch.empty(total, dtype=torch.int32, device=dev).view(torch.uint32)
+    t1 = time.time()
+    plan = icx.Plan(pool.descs(out, out_off), None)  # tune every field on this batch
+    tune = plan.tuning()
+    t2 = time.time()
+    ints = int(L.sum())
+
+    def timed(launch, steps):
+        for _ in range(args.warmup):
+            flush_l2()
+            launch()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush_l2()
+            a.record()
+            launch()
+            b.record()
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        return max_over_ranks(ms, world)
+
+    def verify(what):
+        # every list position written and equal; padding is outside any list
+        outi = out.view(torch.int32)
+        outi[pool.padding] = 0
+        if plan.status() != icx.OK or not torch.equal(out, pool.x):
+            raise SystemExit(f"{what}: verification failed")
+        outi.fill_(-1)
+
+    out.view(torch.int32).fill_(-1)
+    ms_plan = timed(plan.launch, args.batch_steps)
+    verify("batched decode")
+    plan.launch_per_list()  # captures the per-list graph
+    torch.cuda.synchronize()
+    t3 = time.time()
+    ms_each = timed(plan.launch_per_list, max(3, args.batch_steps // 4))
+    verify("per-list decode")
+    comp = pool.nbytes
+    alg = comp + 8 * int(sum(icx.bp128_index_len(int(n)) if c == 0 else icx.fastpfor_index_len(int(n))
+                             for n, c in zip(L, codecs))) + 4 * ints
+    peak, _ = peaks()
+    res = {
+        "workload": f"{len(L)} posting lists, Zipf(1.1) lengths over [128, 2^22] scaled to {ints} ints (reading A), "
+                    f"{int(bp.sum())} SIMD-BP128* (stride 4) / {int((~bp).sum())} SIMD-FastPFOR (stride 1)",
+        "ints": ints, "lists": int(len(L)), "bits_per_int": round(8.0 * comp / ints, 3),
+        "value": round(world * ints / (ms_plan / 1e3) / 1e9, 2), "unit": UNIT, "ms": round(ms_plan, 4),
+        "per_list_value": round(world * ints / (ms_each / 1e3) / 1e9, 2), "per_list_ms": round(ms_each, 4),
+        "ratio_vs_per_list": round(ms_each / ms_plan, 2),
+        "roofline_frac": round(alg / (ms_plan / 1e3) / 1e9 / peak, 4),
+        "tuning": tune, "graph_launches": {"batched": 1, "per_list": int(len(L) + (~bp & (L >= 128)).sum())},
+        "setup_s": {"generate_encode": round(t1 - t0, 1), "plan_tune": round(t2 - t1, 1),
+                    "per_list_capture": round(t3 - t2, 1)},
+    }
+    plan.close()
+    log(f"[bench] batched: {res['value']} Gints/s vs per-list {res['per_list_value']} ({res['ratio_vs_per_list']}x)")
+    return res
 
 
 # --------------------------------------------------------- CPU baseline --
@@ -466,6 +550,10 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
     ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
+    ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
+    ap.add_argument("--batch-lists", type=int, default=65536)
+    ap.add_argument("--batch-total", type=int, default=1 << 28)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

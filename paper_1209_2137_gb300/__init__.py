@@ -419,6 +419,12 @@ class ListPool:
         dst = np.repeat(self.x_off - self.offsets[:-1], self.n) + np.arange(int(self.offsets[-1]), dtype=np.int64)
         host[dst] = np.asarray(values, dtype=np.uint32)[:int(self.offsets[-1])]
         self.x = torch.from_numpy(host.view(np.int32)).to(device).view(torch.uint32)
+        # positions of ``x`` that belong to no list (alignment padding)
+        pad = padded - self.n
+        pad_pos = np.repeat(self.x_off + self.n, pad) + (np.arange(int(pad.sum())) -
+                                                        np.repeat(np.cumsum(pad) - pad, pad))
+        self.padding = torch.from_numpy(np.concatenate([pad_pos, [host.size - 4 + k for k in range(4)]])
+                                        .astype(np.int64)).to(device)
         cap = np.zeros(L, dtype=np.int64)
         ilen = np.zeros(L, dtype=np.int64)
         for i in range(L):

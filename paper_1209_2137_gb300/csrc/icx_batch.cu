@@ -42,7 +42,8 @@ struct __align__(16) ListDev {
     uint32_t units;      // M: metablocks / 16-block units (the tail is unit M)
     uint32_t tail_at;    // index entry where the Variable Byte tail starts
     uint8_t codec, delta, fmt, pad;
-    uint32_t pad2[2];
+    uint32_t item_base;  // its first work item
+    uint32_t pad2;
 };
 static_assert(sizeof(ListDev) == 64, "list record");
 
@@ -70,32 +71,59 @@ static_assert(sizeof(BatchShared) + 8 * kMaxWarps <= kBatchHdr, "batch header");
 
 // ---------------------------------------------------------------- kernels
 
+// Pages of more than kSmallK blocks: one CTA each (items: list, page).
 __global__ void __launch_bounds__(kMetaThreads)
     batch_meta_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ pages,
                       BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
-                      WsHeader* h) {
+                      ulonglong2* __restrict__ ranges, WsHeader* h) {
     __shared__ MetaSmem S;
-    const uint2 pi = pages[blockIdx.x];  // (list, page); slot = blockIdx.x
+    const uint2 pi = pages[blockIdx.x];
     const ListDev& L = lists[pi.x];
     const uint64_t nb = L.n / 128;
     const uint32_t K = (uint32_t)min((uint64_t)kBlocksPerPage, nb - (uint64_t)kBlocksPerPage * pi.y);
-    const size_t g = blockIdx.x;
+    const size_t g = (size_t)L.page_slot + pi.y;
     parse_page(S, L.in, L.in_bytes, L.index[pi.y], L.index[pi.y + 1], K, meta + kBlocksPerPage * g,
-               pmeta + kPageMetaWords * g, umeta + kUnitsPerPage * g, h);
+               pmeta + kPageMetaWords * g, umeta + kUnitsPerPage * g, h,
+               ranges + L.item_base + (size_t)kUnitsPerPage * pi.y);
 }
 
-// Byte range of every SIMD-BP128 work item (for the L2 prefetch ahead).
+// Pages of at most kSmallK blocks: one warp each.
+constexpr int kSmallWarps = 8;
+
+__global__ void __launch_bounds__(kSmallWarps * 32)
+    batch_meta_small_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ pages, uint32_t count,
+                            BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
+                            ulonglong2* __restrict__ ranges, WsHeader* h) {
+    __shared__ SmallPageSmem S[kSmallWarps];
+    const int warp = threadIdx.x >> 5;
+    const uint32_t j = blockIdx.x * kSmallWarps + warp;
+    if (j >= count) return;
+    const uint2 pi = pages[j];
+    const ListDev& L = lists[pi.x];
+    const uint64_t nb = L.n / 128;
+    const uint32_t K = (uint32_t)min((uint64_t)kBlocksPerPage, nb - (uint64_t)kBlocksPerPage * pi.y);
+    const size_t g = (size_t)L.page_slot + pi.y;
+    parse_small_page(S[warp], L.in, L.in_bytes, L.index[pi.y], L.index[pi.y + 1], K, meta + kBlocksPerPage * g,
+                     pmeta + kPageMetaWords * g, umeta + kUnitsPerPage * g, h,
+                     ranges + L.item_base + (size_t)kUnitsPerPage * pi.y);
+}
+
+// Copy range (address, bytes) of every SIMD-BP128 work item: the metablock
+// its index entries delimit, bytes = ~0 if they are invalid.  (SIMD-FastPFOR
+// items get theirs from the page parse of every launch; tails copy nothing.)
 __global__ void batch_ranges_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
                                     ulonglong2* __restrict__ ranges) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nwork) return;
     const uint2 wi = work[i];
     const ListDev& L = lists[wi.x];
+    if (L.codec != ICX_CODEC_BP128 && wi.y < L.units) return;
     ulonglong2 r = make_ulonglong2(0, 0);
-    if (L.codec == ICX_CODEC_BP128 && wi.y < L.units) {
+    if (wi.y < L.units) {
         const uint64_t off = L.index[wi.y], end = L.index[wi.y + 1];
-        if (off <= end && end <= L.in_bytes && end - off <= kMetaMax && ((off | end) & 15) == 0)
-            r = make_ulonglong2(reinterpret_cast<uint64_t>(L.in + off), end - off);
+        const bool ok = off <= end && end <= L.in_bytes && end - off >= 16 && end - off <= kMetaMax &&
+                        ((off | end) & 15) == 0;
+        r = ok ? make_ulonglong2(reinterpret_cast<uint64_t>(L.in + off), end - off) : make_ulonglong2(0, ~0u);
     }
     ranges[i] = r;
 }
@@ -172,8 +200,7 @@ template <int W>
 __global__ void __launch_bounds__(W * 32, 16 / W)
     batch_decode_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
                         const ulonglong2* __restrict__ ranges, const BlockMeta* __restrict__ meta,
-                        const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, bool l2_ahead,
-                        WsHeader* h) {
+                        const uint32_t* __restrict__ pmeta, bool l2_ahead, WsHeader* h) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchShared& S = *reinterpret_cast<BatchShared*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -192,65 +219,57 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     uint32_t phase = 0, it = 0;
     bool broken = false;
 
-    // loads work item i into the warp context and starts its bulk copy;
-    // C.size: bytes in flight (0: none, ~0u: invalid)
-    auto issue = [&](uint32_t i) {
+    // Work item i, step 1: its precomputed copy range; the bulk copy starts
+    // at once.  C.size: bytes in flight (0: none, ~0u: invalid).
+    auto start_copy = [&](uint32_t i) {
         __syncwarp();
-        if (i >= nwork) {
-            if (lane == 0) C.valid = 0;
-            __syncwarp();
-            return;
+        if (lane == 0) {
+            if (i < nwork) {
+                const uint2 wi = work[i];
+                const ulonglong2 rg = ranges[i];
+                const uint32_t size = (uint32_t)rg.y;
+                if (!broken && size != 0 && size != ~0u) {
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, size);
+                    bulk_load(buf, reinterpret_cast<const void*>(rg.x), size, bar);
+                }
+                C.list = wi.x;
+                C.u = wi.y;
+                C.size = size;
+                C.valid = 1;
+            } else {
+                C.valid = 0;
+            }
         }
-        const uint2 wi = work[i];
-        if (lane < 4) reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + wi.x)[lane];
         __syncwarp();
-        const uint32_t u = wi.y, M = C.L.units;
+    };
+    // step 2, while the copy is in flight: the list record and, for a
+    // SIMD-FastPFOR unit, its block records and page offset
+    auto load_context = [&]() {
+        if (!C.valid) return;
+        if (lane < 4) reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + C.list)[lane];
+        __syncwarp();
+        const uint32_t u = C.u, M = C.L.units;
         const uint64_t nb = C.L.n / 128;
         const uint32_t K = u < M ? (uint32_t)min((uint64_t)16, nb - 16 * (uint64_t)u) : 0u;
-        uint32_t size = 0, slot = 0;
-        uint64_t pbase = 0;
         if (u < M && C.L.codec == ICX_CODEC_FASTPFOR) {
             const uint32_t p = u / kUnitsPerPage, q = u % kUnitsPerPage;
-            slot = C.L.page_slot + p;
+            const uint32_t slot = C.L.page_slot + p;
             if ((uint32_t)lane < K)
                 reinterpret_cast<uint4*>(m)[lane] =
                     reinterpret_cast<const uint4*>(meta + (size_t)kBlocksPerPage * slot + 16 * q)[lane];
             if (lane == 0) {
-                const uint2 um = umeta[(size_t)kUnitsPerPage * slot + q];
-                const bool bad = pmeta[(size_t)kPageMetaWords * slot + 32] != 0;
-                pbase = C.L.index[p];
-                size = bad ? ~0u : um.y;
-                if (!broken && !bad && um.y) {
-                    fence_proxy_async();
-                    mbar_expect_tx(bar, um.y);
-                    bulk_load(buf, C.L.in + pbase + um.x, um.y, bar);
-                }
-            }
-        } else if (u < M && lane == 0) {
-            const uint64_t off = C.L.index[u], end = C.L.index[u + 1];
-            const bool ok = off <= end && end <= C.L.in_bytes && end - off >= 16 && end - off <= kMetaMax &&
-                            ((off | end) & 15) == 0;
-            size = ok ? (uint32_t)(end - off) : ~0u;
-            if (ok && !broken) {
-                fence_proxy_async();
-                mbar_expect_tx(bar, size);
-                bulk_load(buf, C.L.in + off, size, bar);
+                C.slot = slot;
+                C.pbase = C.L.index[p];
             }
         }
-        if (lane == 0) {
-            C.list = wi.x;
-            C.u = u;
-            C.K = K;
-            C.size = size;
-            C.slot = slot;
-            C.pbase = pbase;
-            C.valid = 1;
-        }
+        if (lane == 0) C.K = K;
         __syncwarp();
     };
 
     uint32_t tile = S.nx[0];
-    if (tile < ntiles) issue(tile * W + warp);
+    start_copy(tile < ntiles ? tile * W + warp : nwork);
+    load_context();
 
     while (tile < ntiles) {
         const uint32_t i = tile * W + warp;
@@ -277,7 +296,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
                     if (lane == 0) set_error(h, ICX_ETIMEOUT);
                 }
             }
-            if (lane == 0 && pf.y) prefetch_l2(reinterpret_cast<const void*>(pf.x), (uint32_t)pf.y);
+            if (lane == 0 && pf.y && pf.y != ~0ull) prefetch_l2(reinterpret_cast<const void*>(pf.x), (uint32_t)pf.y);
             if (ok) {
                 if (codec == ICX_CODEC_FASTPFOR) {
                     fp_unit_unpack_patch(C.L.in, C.pbase, pmeta + (size_t)kPageMetaWords * C.slot, m, K, buf, blk_of,
@@ -335,10 +354,9 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             first_b = bm ? (uint32_t)(__ffs(bm) - 1) : (uint32_t)W;
             single = bm == 0;
             need_carry = S.start[0] == 0;
-            const uint4 last = shfl4(incl, W - 1);
             // the last list's running sum: a prefix unless it is the tile's
             // first list and that list started in an earlier tile
-            publish_state(h, epoch, tile, last, !(single && need_carry));
+            publish_state(h, epoch, tile, shfl4(incl, W - 1), !(single && need_carry));
         }
         if (valid && delta == ICX_DELTA_1) {
             unit_local_scan<ICX_DELTA_1>(v, Ks, residue, lane);
@@ -369,9 +387,9 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         uint32_t* out = C.L.out;
         const uint64_t n = C.L.n, first = u < M ? 2048 * (uint64_t)u : 128 * (n / 128);
         const uint32_t next = S.nx[it & 1];
-        // (the context is reloaded by issue(); keep what the stores need)
-        issue(next < ntiles ? next * W + warp : nwork);
+        start_copy(next < ntiles ? next * W + warp : nwork);  // lands during the stores
         if (valid && Ks) store_unit(out, first, n, v, Ks, pref, lane);
+        load_context();
         tile = next;
     }
     if (broken) mbar_wait(bar, phase);
@@ -384,7 +402,7 @@ struct PlanMem {
     ListDev* lists = nullptr;
     uint2* work = nullptr;
     ulonglong2* ranges = nullptr;
-    uint2* pages = nullptr;
+    uint2* pages = nullptr;  // large pages, then small pages
     BlockMeta* meta = nullptr;
     uint32_t* pmeta = nullptr;
     uint2* umeta = nullptr;
@@ -421,12 +439,14 @@ struct icx_plan {
     std::vector<icx_list_desc> lists;
     std::vector<ListDev> host_lists;
     std::vector<uint32_t> items_per_list;  // work items of each list
-    size_t nwork = 0, npages = 0, nmini = 0;
+    size_t nwork = 0, npages = 0, nlarge = 0, nsmall = 0, nmini = 0;
     size_t max_n = 0;
     void* mem = nullptr;
     icx::PlanMem d;
     icx_tuning tune{8, 0, 1, nullptr};
-    cudaStream_t cap = nullptr;  // capture stream
+    cudaStream_t cap = nullptr;   // capture stream
+    cudaStream_t cap2 = nullptr;  // second branch of the graph (small pages)
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t exec = nullptr;
     // per-list baseline
     void* single_ws = nullptr;
@@ -490,17 +510,28 @@ cudaError_t capture(icx_plan* p) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    if (p->npages)
-        batch_meta_kernel<<<(unsigned)p->npages, kMetaThreads, 0, p->cap>>>(p->d.lists, p->d.pages, p->d.meta,
-                                                                           p->d.pmeta, p->d.umeta, p->d.ws);
+    // the two page parses run side by side (fork / join inside the graph)
+    if (p->nsmall) {
+        cudaEventRecord(p->fork, p->cap);
+        cudaStreamWaitEvent(p->cap2, p->fork, 0);
+        batch_meta_small_kernel<<<(unsigned)((p->nsmall + kSmallWarps - 1) / kSmallWarps), kSmallWarps * 32, 0,
+                                  p->cap2>>>(p->d.lists, p->d.pages + p->nlarge, (uint32_t)p->nsmall, p->d.meta,
+                                             p->d.pmeta, p->d.umeta, p->d.ranges, p->d.ws);
+        cudaEventRecord(p->join, p->cap2);
+    }
+    if (p->nlarge)
+        batch_meta_kernel<<<(unsigned)p->nlarge, kMetaThreads, 0, p->cap>>>(p->d.lists, p->d.pages, p->d.meta,
+                                                                           p->d.pmeta, p->d.umeta, p->d.ranges,
+                                                                           p->d.ws);
+    if (p->nsmall) cudaStreamWaitEvent(p->cap, p->join, 0);
     if (p->nwork) {
         if (W == 4)
             batch_decode_kernel<4><<<grid, 4 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
-                                                                   p->d.ranges, p->d.meta, p->d.pmeta, p->d.umeta,
+                                                                   p->d.ranges, p->d.meta, p->d.pmeta,
                                                                    p->tune.l2_prefetch != 0, p->d.ws);
         else
             batch_decode_kernel<8><<<grid, 8 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
-                                                                   p->d.ranges, p->d.meta, p->d.pmeta, p->d.umeta,
+                                                                   p->d.ranges, p->d.meta, p->d.pmeta,
                                                                    p->tune.l2_prefetch != 0, p->d.ws);
     }
     cudaError_t le = cudaGetLastError();
@@ -514,7 +545,11 @@ cudaError_t capture(icx_plan* p) {
 cudaError_t apply_order(icx_plan* p, int order) {
     const std::vector<uint2> w = build_work(*p, order);
     if (w.empty()) return cudaSuccess;
-    cudaError_t e = cudaMemcpy(p->d.work, w.data(), w.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    for (size_t i = 0; i < w.size(); ++i)
+        if (w[i].y == 0) p->host_lists[w[i].x].item_base = (uint32_t)i;
+    cudaError_t e = cudaMemcpy(p->d.lists, p->host_lists.data(), sizeof(ListDev) * p->host_lists.size(),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d.work, w.data(), w.size() * sizeof(uint2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     icx::batch_ranges_kernel<<<(unsigned)((w.size() + 255) / 256), 256, 0, p->cap>>>(p->d.lists, p->d.work,
                                                                                     (uint32_t)w.size(), p->d.ranges);
@@ -662,7 +697,7 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
     p->lists.assign(lists, lists + nlists);
     p->host_lists.resize(nlists);
     p->items_per_list.resize(nlists);
-    std::vector<uint2> pages;
+    std::vector<uint2> pages, small_pages;
     std::vector<uint32_t> mini_ids;
     for (size_t i = 0; i < nlists; ++i) {
         const icx_list_desc& l = lists[i];
@@ -680,9 +715,13 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
         d.fmt = (uint8_t)(l.codec == ICX_CODEC_BP128 ? l.fmt : 0);
         if (l.codec == ICX_CODEC_FASTPFOR) {
             const size_t P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
-            d.page_slot = (uint32_t)pages.size();
+            d.page_slot = (uint32_t)p->npages;
             d.tail_at = (uint32_t)P;
-            for (size_t q = 0; q < P; ++q) pages.push_back(make_uint2((uint32_t)i, (uint32_t)q));
+            for (size_t q = 0; q < P; ++q) {
+                const size_t K = std::min<size_t>(kBlocksPerPage, nb - kBlocksPerPage * q);
+                (K > kSmallK ? pages : small_pages).push_back(make_uint2((uint32_t)i, (uint32_t)q));
+            }
+            p->npages += P;
         } else {
             d.tail_at = (uint32_t)M;
         }
@@ -691,7 +730,9 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
         p->nwork += p->items_per_list[i];
         p->max_n = std::max(p->max_n, l.n);
     }
-    p->npages = pages.size();
+    p->nlarge = pages.size();
+    p->nsmall = small_pages.size();
+    pages.insert(pages.end(), small_pages.begin(), small_pages.end());
     p->nmini = mini_ids.size();
     if (p->nwork > 0xFFFFFFF0ull / 2) {
         delete p;
@@ -732,12 +773,16 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
         icx_plan_destroy(p);
         return st;
     };
-    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(ICX_ECUDA);
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(ICX_ECUDA);
     if (nlists &&
         cudaMemcpy(p->d.lists, p->host_lists.data(), sizeof(ListDev) * nlists, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(ICX_ECUDA);
-    if (p->npages &&
-        cudaMemcpy(p->d.pages, pages.data(), sizeof(uint2) * p->npages, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (!pages.empty() &&
+        cudaMemcpy(p->d.pages, pages.data(), sizeof(uint2) * pages.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(ICX_ECUDA);
     if (cudaMemset(p->d.ws, 0, kWsHeaderBytes + 32 * (ntiles_max + 16)) != cudaSuccess) return fail(ICX_ECUDA);
     if (p->nmini) {
@@ -874,6 +919,9 @@ void icx_plan_destroy(icx_plan* p) {
         cudaStreamSynchronize(p->cap);
         cudaStreamDestroy(p->cap);
     }
+    if (p->cap2) cudaStreamDestroy(p->cap2);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
     if (p->mem) cudaFree(p->mem);
     if (p->single_ws) cudaFree(p->single_ws);
     delete p;

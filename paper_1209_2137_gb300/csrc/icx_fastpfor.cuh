@@ -53,13 +53,73 @@ __device__ __forceinline__ uint32_t rec_len(uint32_t b, uint32_t mb, uint32_t c)
     return mb > b ? 3u + min(c, 129u) : 2u;
 }
 
+// Whole warp: the exception arrays after a page's byte array.  Their offsets
+// follow from the page's per-width counts (lane d-1 holds cnt_total of
+// width d); lane d-1 checks the stored count of array d against it, and the
+// arrays must end exactly at the page end.  Writes the page record pg (array
+// offsets, then the flag word) and returns the warp-uniform `bad`.
+__device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize, uint32_t bytes_at, uint32_t Lpad,
+                                            uint32_t cnt_total, bool bad, uint32_t* __restrict__ pg, WsHeader* h,
+                                            int lane) {
+    uint32_t my_off = 0, my_cnt_at = 0;
+    if (!bad) {
+        const uint32_t bitset = ld32(page + bytes_at + Lpad);
+        uint64_t q = (uint64_t)bytes_at + Lpad + 4;
+        for (int d = 1; d <= 32; ++d) {
+            const uint32_t nd = __shfl_sync(FULL, cnt_total, d - 1);
+            if (!((bitset >> (d - 1)) & 1u)) {
+                if (nd) bad = true;
+                continue;
+            }
+            if (lane == d - 1) {
+                my_cnt_at = (uint32_t)q;
+                my_off = (uint32_t)pad_up(q + 4, 16);
+            }
+            q = pad_up(q + 4, 16) + 16 * (uint64_t)d * ((nd + 127) / 128);
+            if (q > psize) {
+                bad = true;
+                break;
+            }
+        }
+        if (pad_up(q, 16) != psize) bad = true;
+        if (!bad && ((bitset >> lane) & 1u) && ld32(page + my_cnt_at) != cnt_total) bad = true;
+    }
+    bad = __any_sync(FULL, bad);
+    pg[lane] = bad ? 0u : my_off;
+    if (lane == 0) pg[32] = bad ? 1u : 0u;
+    if (bad && lane == 0) set_error(h, ICX_ECORRUPT);
+    return bad;
+}
+
+// Exclusive count, per block, of the earlier exceptions of the same width d
+// within one warp round (lane = block; d = 0: no exceptions), added to
+// `base` = the lane-(d-1) running count before the round; lane d-1 of `cnt`
+// then advances by the round's total of width d.  Width by width (the
+// distinct widths of a round are few).
+__device__ __forceinline__ uint32_t round_cursor(uint32_t d, uint32_t c, uint32_t& cnt, int lane) {
+    uint32_t within = __shfl_sync(FULL, cnt, d ? (d - 1) & 31 : 0);
+    uint32_t pend = __ballot_sync(FULL, d != 0 && d <= 32);
+    while (pend) {
+        const uint32_t dl = __shfl_sync(FULL, d, __ffs(pend) - 1);
+        const bool mine = d == dl;
+        const uint32_t x = mine ? c : 0u;
+        const uint32_t sc = warp_incl_scan(x, lane);
+        if (mine) within += sc - x;
+        const uint32_t tot = __shfl_sync(FULL, sc, 31);
+        if ((uint32_t)lane == dl - 1) cnt += tot;
+        pend &= ~__ballot_sync(FULL, mine);
+    }
+    return within;
+}
+
 // Parses one page, CTA-wide (kMetaThreads threads): the page occupies
 // in[base, end) and holds K blocks; writes the K block records to pm, the
 // exception-array offsets and the page flag to pg, and per unit of 16
 // blocks its packed range to um.
 __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restrict__ in, size_t in_bytes,
                                            uint64_t base, uint64_t end, uint32_t K, BlockMeta* __restrict__ pm,
-                                           uint32_t* __restrict__ pg, uint2* __restrict__ um, WsHeader* h) {
+                                           uint32_t* __restrict__ pg, uint2* __restrict__ um, WsHeader* h,
+                                           ulonglong2* __restrict__ rng = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint8_t* sb = reinterpret_cast<const uint8_t*>(S.bytes);
     const uint8_t* s1 = reinterpret_cast<const uint8_t*>(S.j1);
@@ -184,19 +244,7 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         const uint32_t incl = warp_incl_scan(bb, lane);
         pk[i] = run + incl - bb;
         run += __shfl_sync(FULL, incl, 31);
-        // exclusive count of earlier exceptions of the same width, one width at a time
-        uint32_t within = __shfl_sync(FULL, cnt, d ? (d - 1) & 31 : 0);
-        uint32_t pend = __ballot_sync(FULL, d != 0 && d <= 32);
-        while (pend) {
-            const uint32_t dl = __shfl_sync(FULL, d, __ffs(pend) - 1);
-            const bool mine = d == dl;
-            const uint32_t x = mine ? c : 0u;
-            const uint32_t sc = warp_incl_scan(x, lane);
-            if (mine) within += sc - x;
-            const uint32_t tot = __shfl_sync(FULL, sc, 31);
-            if ((uint32_t)lane == dl - 1) cnt += tot;
-            pend &= ~__ballot_sync(FULL, mine);
-        }
+        const uint32_t within = round_cursor(d, c, cnt, lane);
         b_[i] = bb;
         d_[i] = d;
         c_[i] = c;
@@ -234,47 +282,118 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
             }
         }
     }
-    // ---- exception arrays (warp 0): offsets follow from the page's counts;
-    // lane d-1 checks the stored count of array d against the records
-    if (warp == 0) {
-        uint32_t my_off = 0, my_cnt_at = 0;
-        if (!bad) {
-            const uint32_t bitset = ld32(page + bytes_at + Lpad);
-            uint64_t q = (uint64_t)bytes_at + Lpad + 4;
-            for (int d = 1; d <= 32; ++d) {
-                const uint32_t nd = __shfl_sync(FULL, cnt_total, d - 1);
-                if (!((bitset >> (d - 1)) & 1u)) {
-                    if (nd) bad = true;
-                    continue;
-                }
-                if (lane == d - 1) {
-                    my_cnt_at = (uint32_t)q;
-                    my_off = (uint32_t)pad_up(q + 4, 16);
-                }
-                q = pad_up(q + 4, 16) + 16 * (uint64_t)d * ((nd + 127) / 128);
-                if (q > psize) {
-                    bad = true;
-                    break;
-                }
-            }
-            if (pad_up(q, 16) != psize) bad = true;
-            if (!bad && ((bitset >> lane) & 1u) && ld32(page + my_cnt_at) != cnt_total) bad = true;
-            bad = __any_sync(FULL, bad);
-        }
-        pg[lane] = bad ? 0u : my_off;
-        if (lane == 0) pg[32] = bad ? 1u : 0u;
-        if (bad && lane == 0) set_error(h, ICX_ECORRUPT);
-    }
+    // ---- exception arrays (warp 0)
+    if (warp == 0) bad = page_arrays(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
     __syncthreads();
     // per unit of 16 blocks: where its packed low bits start and how long they are
     const uint32_t nunits = (K + 15) / 16;
-    if (!bad && (uint32_t)tid < nunits) {
-        const uint32_t k0 = 16 * tid, k1 = min(K, k0 + 16) - 1;
-        const uint32_t first = S.poff[k0];
-        um[tid] = make_uint2(first, S.poff[k1] + 16 * (S.bmc[k1] & 0xFF) - first);
+    if ((uint32_t)tid < nunits) {
+        uint2 x = make_uint2(0, ~0u);
+        if (!bad) {
+            const uint32_t k0 = 16 * tid, k1 = min(K, k0 + 16) - 1;
+            const uint32_t first = S.poff[k0];
+            x = make_uint2(first, S.poff[k1] + 16 * (S.bmc[k1] & 0xFF) - first);
+            um[tid] = x;
+        }
+        if (rng) rng[tid] = make_ulonglong2(bad ? 0ull : reinterpret_cast<uint64_t>(page + x.x), x.y);
     }
 }
 
+
+// ------------------------------------------------------ small-page parse
+//
+// One warp per page of at most kSmallK blocks (short lists): the byte array
+// prefix that K records can occupy is staged in shared memory, lane 0 walks
+// the K record starts there, then one lane per block does what one round of
+// the CTA parse does.
+
+constexpr uint32_t kSmallK = 32;
+constexpr uint32_t kSmallWin = kSmallK * kRecMax + 16;  // every record of <= 32 blocks
+
+struct SmallPageSmem {
+    uint32_t bytes[kSmallWin / 4 + 4];
+    uint32_t start[kSmallK];
+};
+
+__device__ __forceinline__ void parse_small_page(SmallPageSmem& S, const uint8_t* __restrict__ in, size_t in_bytes,
+                                                 uint64_t base, uint64_t end, uint32_t K,
+                                                 BlockMeta* __restrict__ pm, uint32_t* __restrict__ pg,
+                                                 uint2* __restrict__ um, WsHeader* h,
+                                                 ulonglong2* __restrict__ rng = nullptr) {
+    const int lane = threadIdx.x & 31;
+    const uint8_t* sb = reinterpret_cast<const uint8_t*>(S.bytes);
+    bool bad = !(base <= end && end <= in_bytes && (base & 15) == 0 && end - base >= 16);
+    const uint8_t* page = in + base;
+    const uint32_t psize = bad ? 0u : (uint32_t)min(end - base, (uint64_t)0xFFFFFFF0u);
+    uint32_t len_at = 0, L = 0, bytes_at = 0;
+    if (!bad) {
+        len_at = 4 * ld32(page);
+        bad = len_at < 16 || (len_at & 15) || (uint64_t)len_at + 4 > psize;
+    }
+    if (!bad) {
+        L = ld32(page + len_at);
+        bytes_at = len_at + 4;
+        bad = (uint64_t)bytes_at + pad_up(L, 4) + 4 > psize;
+    }
+    const uint32_t Lpad = bad ? 0u : (uint32_t)pad_up(L, 4);
+    const uint32_t* arr = reinterpret_cast<const uint32_t*>(page + bytes_at);
+    const uint32_t nw = min(kSmallWin, Lpad) / 4;
+    for (uint32_t i = lane; i < kSmallWin / 4 + 4; i += 32) S.bytes[i] = i < nw ? __ldg(arr + i) : 0u;
+    __syncwarp();
+    if (lane == 0 && !bad) {
+        // K <= 32 records of <= kRecMax bytes: every start stays in the window
+        uint32_t r = 0;
+        for (uint32_t k = 0; k < K; ++k) {
+            if (r + 2 > L) {
+                bad = true;
+                break;
+            }
+            S.start[k] = r;
+            r += rec_len(sb[r], sb[r + 1], sb[r + 2]);
+        }
+    }
+    bad = __shfl_sync(FULL, bad, 0);
+    __syncwarp();
+    const bool valid = !bad && (uint32_t)lane < K;
+    uint32_t b = 0, mb = 0, c = 0, st = 0;
+    if (valid) {
+        st = S.start[lane];
+        b = sb[st];
+        mb = sb[st + 1];
+        c = sb[st + 2];
+    }
+    const uint32_t d = mb > b ? mb - b : 0u;
+    if (!d) c = 0;
+    bool rbad = valid && (b > 32 || mb > 32 || mb < b || c > 128 || (uint64_t)st + (d ? 3 + c : 2) > L);
+    const uint32_t bb = b <= 32 ? b : 0u;
+    const uint32_t incl = warp_incl_scan(bb, lane);
+    const uint32_t packed_total = __shfl_sync(FULL, incl, 31);
+    uint32_t cnt = 0;
+    const uint32_t cursor = round_cursor(d, c, cnt, lane);
+    bad = __any_sync(FULL, bad || rbad) || (!bad && 16 + 16 * packed_total != len_at);
+    const uint32_t poff = 16 + 16 * (incl - bb);
+    if (!bad && valid) {
+        BlockMeta m;
+        m.packed_off = poff;
+        m.pos_off = d ? bytes_at + st + 3 : 0u;
+        m.cursor = d ? cursor : 0u;
+        m.b = (uint8_t)bb;
+        m.d = (uint8_t)d;
+        m.c = (uint8_t)c;
+        m.flags = 0;
+        pm[lane] = m;
+    }
+    bad = page_arrays(page, psize, bytes_at, Lpad, cnt, bad, pg, h, lane);
+    // per unit of 16 blocks (at most two): its packed range
+    const uint32_t k0 = 16 * (uint32_t)(lane & 1), k1 = min(K, k0 + 16) - 1;
+    const uint32_t f0 = __shfl_sync(FULL, poff, (int)k0), f1 = __shfl_sync(FULL, poff, (int)(k1 & 31)),
+                   b1 = __shfl_sync(FULL, bb, (int)(k1 & 31));
+    if (lane < 2 && k0 < K) {
+        const uint2 x = bad ? make_uint2(0, ~0u) : make_uint2(f0, f1 + 16 * b1 - f0);
+        if (!bad) um[lane] = x;
+        if (rng) rng[lane] = make_ulonglong2(bad ? 0ull : reinterpret_cast<uint64_t>(page + x.x), x.y);
+    }
+}
 
 // ---------------------------------------------------------- unit decode
 
