@@ -285,6 +285,52 @@ icx_status icx_plan_tuning(const icx_plan *plan, icx_tuning *out);
 /* Frees the plan's device memory and graphs. */
 void icx_plan_destroy(icx_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Serving loop: a pool of lists resident in device memory (with their
+ * indexes and, for SIMD-FastPFOR, page records parsed once at creation)
+ * answers requests for several lists each.  No counterpart in the paper.
+ *
+ * A request is admitted, first come first served, when its decode buffers
+ * (4 bytes per integer of its lists, each list 16-byte aligned) fit in the
+ * budget; admitted requests are batched onto whichever of the server's
+ * streams is free (continuous batching: a batch is launched as soon as a
+ * stream is free, so batches overlap on the device) and decoded by one
+ * launch of the batched kernel per batch.  A request completes when the
+ * host observes its batch's completion event; its buffers are freed then.
+ * ---------------------------------------------------------------------- */
+
+typedef struct icx_server icx_server;
+
+typedef struct {
+    uint64_t requests;        /* completed */
+    uint64_t ints;            /* integers decoded */
+    uint64_t batches;         /* kernel launches */
+    uint64_t max_batch;       /* most requests in one batch */
+    uint64_t max_queue;       /* most requests waiting for admission */
+    uint64_t peak_bytes;      /* most decode-buffer bytes in use */
+    double wall_s;            /* first arrival to last completion */
+} icx_server_stats;
+
+/* Creates a server over `pool` (d_out ignored; every other field as for a
+ * plan) with `budget_bytes` of decode buffers allocated once and `streams`
+ * (>= 2) streams.  warps_per_cta: 4 or 8.  Synchronous. */
+icx_status icx_server_create(const icx_list_desc *pool, size_t nlists, size_t budget_bytes, int streams,
+                             int warps_per_cta, icx_server **server);
+
+/* Serves an open-loop request schedule and returns when every request has
+ * completed.  Request r arrives arrival_ns[r] nanoseconds after the start
+ * (non-decreasing) and asks for the lists ids[offs[r] .. offs[r+1]) (pool
+ * indexes).  latency_ns[r] receives its completion time minus its arrival
+ * time.  If results is not NULL, request r's lists are copied, decoded and
+ * back to back without padding, to results + res_off[r] (host memory; slow,
+ * for checks).  A request larger than the whole budget fails with
+ * ICX_ENOSPC before anything runs; data errors are returned after the run. */
+icx_status icx_server_run(icx_server *server, size_t nreq, const uint64_t *arrival_ns, const uint64_t *offs,
+                          const uint32_t *ids, uint64_t *latency_ns, uint32_t *results, const uint64_t *res_off,
+                          icx_server_stats *stats);
+
+void icx_server_destroy(icx_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,9 @@ def lib():
                 "icx_plan_status": ([vp, vp, ctypes.POINTER(ctypes.c_int)], i),
                 "icx_plan_tuning": ([vp, vp], i),
                 "icx_plan_destroy": ([vp], None),
+                "icx_server_create": ([vp, sz, sz, i, i, ctypes.POINTER(vp)], i),
+                "icx_server_run": ([vp, sz, vp, vp, vp, vp, vp, vp, vp], i),
+                "icx_server_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -92,7 +95,7 @@ EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_byte
             "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "delta_decode", "delta_encode",
             "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning", "icx_plan_create",
             "icx_plan_error_list", "icx_plan_launch", "icx_plan_launch_per_list", "icx_plan_status", "icx_plan_tuning",
-            "icx_plan_destroy")
+            "icx_plan_destroy", "icx_server_create", "icx_server_run", "icx_server_destroy")
 
 
 def _check(code: int, what: str):
@@ -484,4 +487,68 @@ class ListPool:
                                 int(self.n[i]), (bi + 8 * int(self.index_off[i])) if with_index else None,
                                 int(self.codecs[i]), int(self.deltas[i]), int(self.fmts[i])))
         return res
+
+
+# -- serving loop -----------------------------------------------------------------
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("ints", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("max_batch", ctypes.c_uint64), ("max_queue", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("wall_s", ctypes.c_double)]
+
+
+class Server:
+    """The serving loop (icx_server_*) over a resident pool of lists.
+
+    ``descs``: ListDesc per pool list (d_out ignored); the buffers they point
+    to must outlive the server."""
+
+    def __init__(self, descs, budget_bytes: int = 16 << 30, streams: int = 2, warps_per_cta: int = 8):
+        arr = (ListDesc * len(descs))(*descs)
+        self._keep = arr
+        handle = ctypes.c_void_p()
+        code = lib().icx_server_create(ctypes.cast(arr, ctypes.c_void_p), len(descs), budget_bytes, streams,
+                                       warps_per_cta, ctypes.byref(handle))
+        if code != OK:
+            bad = lib().icx_plan_error_list()
+            raise IcxError(code, "icx_server_create" + (f" (list {bad})" if bad >= 0 else ""))
+        self._h = handle
+
+    def run(self, arrival_ns, req_offsets, list_ids, results=False):
+        """Serves the schedule; returns (latency_ns per request, stats dict,
+        results or None).  With results=True every request's lists come back
+        decoded, back to back (a list of numpy arrays, one per request)."""
+        import numpy as np
+        arrival = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+        offs = np.ascontiguousarray(req_offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(list_ids, dtype=np.uint32)
+        nreq = arrival.size
+        lat = np.zeros(nreq, dtype=np.uint64)
+        stats = ServerStats()
+        res = res_off = None
+        if results:
+            n = np.array([d.n for d in self._keep], dtype=np.uint64)
+            per = np.array([int(n[ids[offs[r]:offs[r + 1]]].sum()) for r in range(nreq)], dtype=np.uint64)
+            res_off = np.zeros(nreq, dtype=np.uint64)
+            np.cumsum(per[:-1], out=res_off[1:])
+            res = np.zeros(int(per.sum()) + 1, dtype=np.uint32)
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+        _check(lib().icx_server_run(self._h, nreq, vp(arrival), vp(offs), vp(ids), vp(lat), vp(res), vp(res_off),
+                                    ctypes.cast(ctypes.pointer(stats), ctypes.c_void_p)), "icx_server_run")
+        st = {f: getattr(stats, f) for f, _ in ServerStats._fields_}
+        out = None
+        if results:
+            out = [res[int(res_off[r]):int(res_off[r]) + int(per[r])] for r in range(nreq)]
+        return lat, st, out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().icx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

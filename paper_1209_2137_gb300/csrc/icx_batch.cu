@@ -22,7 +22,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -196,11 +199,30 @@ __device__ __forceinline__ void publish_state(WsHeader* h, uint32_t epoch, uint3
                    ((unsigned long long)tag << 32) | comp(v, lane));
 }
 
-template <int W>
+// A decode instance of the serving loop: one list of one request, decoded
+// into that request's buffer.
+struct InstDev {
+    uint32_t list, pad;
+    uint32_t* out;
+};
+// A work item of the serving loop, built on the host: the unit's copy range,
+// its instance and unit index.
+struct __align__(16) ServeItem {
+    uint64_t src;
+    uint32_t size, inst, u, pad;
+    uint64_t pad2;
+};
+static_assert(sizeof(ServeItem) == 32, "serve item");
+
+// SERVE = false: work items are (list, unit) of a plan with per-item copy
+// ranges; SERVE = true: serving-loop items (ServeItem) whose instances
+// (InstDev) name the list and the output, segments are instances.
+template <int W, bool SERVE>
 __global__ void __launch_bounds__(W * 32, 16 / W)
     batch_decode_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
                         const ulonglong2* __restrict__ ranges, const BlockMeta* __restrict__ meta,
-                        const uint32_t* __restrict__ pmeta, bool l2_ahead, WsHeader* h) {
+                        const uint32_t* __restrict__ pmeta, bool l2_ahead, WsHeader* h,
+                        const ServeItem* __restrict__ items = nullptr, const InstDev* __restrict__ insts = nullptr) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchShared& S = *reinterpret_cast<BatchShared*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -225,16 +247,29 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         __syncwarp();
         if (lane == 0) {
             if (i < nwork) {
-                const uint2 wi = work[i];
-                const ulonglong2 rg = ranges[i];
-                const uint32_t size = (uint32_t)rg.y;
+                uint32_t a, u, size;
+                uint64_t src;
+                if constexpr (SERVE) {
+                    const ServeItem it_ = items[i];
+                    a = it_.inst;
+                    u = it_.u;
+                    size = it_.size;
+                    src = it_.src;
+                } else {
+                    const uint2 wi = work[i];
+                    const ulonglong2 rg = ranges[i];
+                    a = wi.x;
+                    u = wi.y;
+                    size = (uint32_t)rg.y;
+                    src = rg.x;
+                }
                 if (!broken && size != 0 && size != ~0u) {
                     fence_proxy_async();
                     mbar_expect_tx(bar, size);
-                    bulk_load(buf, reinterpret_cast<const void*>(rg.x), size, bar);
+                    bulk_load(buf, reinterpret_cast<const void*>(src), size, bar);
                 }
-                C.list = wi.x;
-                C.u = wi.y;
+                C.list = a;
+                C.u = u;
                 C.size = size;
                 C.valid = 1;
             } else {
@@ -247,7 +282,15 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     // SIMD-FastPFOR unit, its block records and page offset
     auto load_context = [&]() {
         if (!C.valid) return;
-        if (lane < 4) reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + C.list)[lane];
+        if constexpr (SERVE) {
+            const InstDev in_ = insts[C.list];
+            if (lane < 4) reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + in_.list)[lane];
+            __syncwarp();
+            if (lane == 0) C.L.out = in_.out;
+        } else {
+            if (lane < 4)
+                reinterpret_cast<uint4*>(&C.L)[lane] = reinterpret_cast<const uint4*>(lists + C.list)[lane];
+        }
         __syncwarp();
         const uint32_t u = C.u, M = C.L.units;
         const uint64_t nb = C.L.n / 128;
@@ -282,7 +325,14 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         uint32_t Ks = 0;  // blocks to scan and store
         bool residue = false;
         ulonglong2 pf = make_ulonglong2(0, 0);
-        if (l2_ahead && lane == 0 && i + gridDim.x * W < nwork) pf = ranges[i + gridDim.x * W];
+        if (l2_ahead && lane == 0 && i + gridDim.x * W < nwork) {
+            if constexpr (SERVE) {
+                const ServeItem& a = items[i + gridDim.x * W];
+                pf = make_ulonglong2(a.src, a.size);
+            } else {
+                pf = ranges[i + gridDim.x * W];
+            }
+        }
         if (valid && u < M) {
             Ks = K;
             bool ok = size != ~0u && !broken;
@@ -418,13 +468,13 @@ static cudaError_t batch_occupancy(int W, int* blocks, int* sms) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
     if (W == 4) {
-        e = cudaFuncSetAttribute(batch_decode_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(batch_decode_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<4>, W * 32, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<4, false>, W * 32, smem);
     } else {
-        e = cudaFuncSetAttribute(batch_decode_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(batch_decode_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<8>, W * 32, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<8, false>, W * 32, smem);
     }
     if (*blocks < 1) *blocks = 1;
     return e;
@@ -474,6 +524,39 @@ icx_status check_list(const icx_list_desc& l) {
         if (!small) return ICX_EINVAL;
     }
     return ICX_OK;
+}
+
+// Fills the device record of list i, appends its pages (more than kSmallK
+// blocks: `large`, else `small`; slots counted by npages) and, without an
+// index, its id to mini_ids.  Returns its work items (units, then the tail).
+uint32_t layout_list(const icx_list_desc& l, uint32_t i, ListDev& d, size_t& npages, std::vector<uint2>& large,
+                     std::vector<uint2>& small, std::vector<uint32_t>& mini_ids) {
+    using namespace icx;
+    std::memset(&d, 0, sizeof d);
+    const size_t nb = l.n / 128, M = (nb + 15) / 16;
+    d.in = l.d_in;
+    d.in_bytes = l.d_in ? l.in_bytes : 0;
+    d.out = l.d_out;
+    d.n = l.n;
+    d.index = l.d_index;
+    d.units = (uint32_t)M;
+    d.codec = (uint8_t)l.codec;
+    d.delta = (uint8_t)l.delta;
+    d.fmt = (uint8_t)(l.codec == ICX_CODEC_BP128 ? l.fmt : 0);
+    if (l.codec == ICX_CODEC_FASTPFOR) {
+        const size_t P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
+        d.page_slot = (uint32_t)npages;
+        d.tail_at = (uint32_t)P;
+        for (size_t q = 0; q < P; ++q) {
+            const size_t K = std::min<size_t>(kBlocksPerPage, nb - kBlocksPerPage * q);
+            (K > kSmallK ? large : small).push_back(make_uint2(i, (uint32_t)q));
+        }
+        npages += P;
+    } else {
+        d.tail_at = (uint32_t)M;
+    }
+    if (l.n && !l.d_index) mini_ids.push_back(i);
+    return l.n ? (uint32_t)(M + (l.n % 128 ? 1 : 0)) : 0u;
 }
 
 // work-list: lists contiguous, in the tuned order
@@ -526,11 +609,11 @@ cudaError_t capture(icx_plan* p) {
     if (p->nsmall) cudaStreamWaitEvent(p->cap, p->join, 0);
     if (p->nwork) {
         if (W == 4)
-            batch_decode_kernel<4><<<grid, 4 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
+            batch_decode_kernel<4, false><<<grid, 4 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
                                                                    p->d.ranges, p->d.meta, p->d.pmeta,
                                                                    p->tune.l2_prefetch != 0, p->d.ws);
         else
-            batch_decode_kernel<8><<<grid, 8 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
+            batch_decode_kernel<8, false><<<grid, 8 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
                                                                    p->d.ranges, p->d.meta, p->d.pmeta,
                                                                    p->tune.l2_prefetch != 0, p->d.ws);
     }
@@ -700,35 +783,10 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
     std::vector<uint2> pages, small_pages;
     std::vector<uint32_t> mini_ids;
     for (size_t i = 0; i < nlists; ++i) {
-        const icx_list_desc& l = lists[i];
-        ListDev& d = p->host_lists[i];
-        std::memset(&d, 0, sizeof d);
-        const size_t nb = l.n / 128, M = (nb + 15) / 16;
-        d.in = l.d_in;
-        d.in_bytes = l.d_in ? l.in_bytes : 0;
-        d.out = l.d_out;
-        d.n = l.n;
-        d.index = l.d_index;
-        d.units = (uint32_t)M;
-        d.codec = (uint8_t)l.codec;
-        d.delta = (uint8_t)l.delta;
-        d.fmt = (uint8_t)(l.codec == ICX_CODEC_BP128 ? l.fmt : 0);
-        if (l.codec == ICX_CODEC_FASTPFOR) {
-            const size_t P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
-            d.page_slot = (uint32_t)p->npages;
-            d.tail_at = (uint32_t)P;
-            for (size_t q = 0; q < P; ++q) {
-                const size_t K = std::min<size_t>(kBlocksPerPage, nb - kBlocksPerPage * q);
-                (K > kSmallK ? pages : small_pages).push_back(make_uint2((uint32_t)i, (uint32_t)q));
-            }
-            p->npages += P;
-        } else {
-            d.tail_at = (uint32_t)M;
-        }
-        if (l.n && !l.d_index) mini_ids.push_back((uint32_t)i);
-        p->items_per_list[i] = l.n ? (uint32_t)(M + (l.n % 128 ? 1 : 0)) : 0u;
+        p->items_per_list[i] = layout_list(lists[i], (uint32_t)i, p->host_lists[i], p->npages, pages, small_pages,
+                                           mini_ids);
         p->nwork += p->items_per_list[i];
-        p->max_n = std::max(p->max_n, l.n);
+        p->max_n = std::max(p->max_n, lists[i].n);
     }
     p->nlarge = pages.size();
     p->nsmall = small_pages.size();
@@ -925,6 +983,413 @@ void icx_plan_destroy(icx_plan* p) {
     if (p->mem) cudaFree(p->mem);
     if (p->single_ws) cudaFree(p->single_ws);
     delete p;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- serving
+
+namespace {
+
+// First-fit allocator of decode buffers inside the server's arena.
+class Arena {
+   public:
+    void reset(size_t bytes) {
+        free_.clear();
+        free_[0] = bytes;
+        used_ = peak_ = 0;
+    }
+    // offset of a block of `bytes` (a multiple of 256), or SIZE_MAX
+    size_t alloc(size_t bytes) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t at = it->first, rest = it->second - bytes;
+            free_.erase(it);
+            if (rest) free_[at + bytes] = rest;
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return at;
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t at, size_t bytes) {
+        used_ -= bytes;
+        auto next = free_.lower_bound(at);
+        if (next != free_.end() && at + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == at) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[at] = bytes;
+    }
+    size_t peak() const { return peak_; }
+
+   private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0, peak_ = 0;
+};
+
+constexpr size_t kServeMaxItems = (size_t)1 << 20;  // work items of one batch
+constexpr size_t kServeMaxInsts = (size_t)1 << 18;  // (request, list) pairs of one batch
+
+size_t pad256(size_t x) { return (x + 255) / 256 * 256; }
+size_t out_bytes(size_t n) { return (4 * n + 15) / 16 * 16; }
+
+}  // namespace
+
+struct icx_server {
+    int device = 0, W = 8, blocks = 1, sms = 1;
+    size_t nlists = 0, budget = 0;
+    std::vector<ListDev> host_lists;
+    std::vector<uint32_t> items;            // work items per list
+    std::vector<uint32_t> item_base;        // first unit of each list in the pool order
+    std::vector<ulonglong2> unit_ranges;    // copy range of every unit, pool order
+    void* mem = nullptr;                    // lists, page records, ranges, mini index
+    icx::PlanMem d;
+    uint8_t* arena = nullptr;
+    Arena alloc;
+    struct Lane {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        icx::WsHeader* ws = nullptr;
+        icx::ServeItem* d_items = nullptr;
+        icx::InstDev* d_insts = nullptr;
+        icx::ServeItem* h_items = nullptr;
+        icx::InstDev* h_insts = nullptr;
+        bool busy = false;
+        std::vector<uint32_t> reqs;
+        std::vector<size_t> offs;
+    };
+    std::vector<Lane> lanes;
+    void* lane_mem = nullptr;
+};
+
+extern "C" {
+
+void icx_server_destroy(icx_server* sv) {
+    if (!sv) return;
+    for (auto& l : sv->lanes) {
+        if (l.st) {
+            cudaStreamSynchronize(l.st);
+            cudaStreamDestroy(l.st);
+        }
+        if (l.ev) cudaEventDestroy(l.ev);
+        if (l.h_items) cudaFreeHost(l.h_items);
+        if (l.h_insts) cudaFreeHost(l.h_insts);
+    }
+    if (sv->lane_mem) cudaFree(sv->lane_mem);
+    if (sv->arena) cudaFree(sv->arena);
+    if (sv->mem) cudaFree(sv->mem);
+    delete sv;
+}
+
+icx_status icx_server_create(const icx_list_desc* pool, size_t nlists, size_t budget_bytes, int streams,
+                             int warps_per_cta, icx_server** out) {
+    using namespace icx;
+    g_error_list = -1;
+    if (!out || (!pool && nlists) || streams < 2 || streams > 16 || budget_bytes < 256 ||
+        (warps_per_cta != 4 && warps_per_cta != 8) || nlists >= 0x80000000u)
+        return ICX_EINVAL;
+    *out = nullptr;
+    for (size_t i = 0; i < nlists; ++i) {
+        icx_list_desc l = pool[i];
+        l.d_out = reinterpret_cast<uint32_t*>(uintptr_t(256));  // outputs come from the arena
+        const icx_status st = check_list(l);
+        if (st != ICX_OK) {
+            g_error_list = (long long)i;
+            return st;
+        }
+    }
+    icx_server* sv = new icx_server();
+    auto fail = [&](icx_status st) {
+        icx_server_destroy(sv);
+        return st;
+    };
+    cudaGetDevice(&sv->device);
+    sv->nlists = nlists;
+    sv->budget = budget_bytes / 256 * 256;
+    sv->W = warps_per_cta;
+    sv->host_lists.resize(nlists);
+    sv->items.resize(nlists);
+    sv->item_base.resize(nlists);
+    std::vector<uint2> pages, small_pages;
+    std::vector<uint32_t> mini_ids;
+    size_t npages = 0, nunits = 0;
+    for (size_t i = 0; i < nlists; ++i) {
+        sv->items[i] = layout_list(pool[i], (uint32_t)i, sv->host_lists[i], npages, pages, small_pages, mini_ids);
+        sv->host_lists[i].out = nullptr;
+        sv->host_lists[i].item_base = (uint32_t)nunits;
+        sv->item_base[i] = (uint32_t)nunits;
+        nunits += sv->items[i];
+    }
+    if (nunits >= 0x80000000ull) return fail(ICX_EINVAL);
+    const size_t nlarge = pages.size(), nsmall = small_pages.size();
+    pages.insert(pages.end(), small_pages.begin(), small_pages.end());
+    std::vector<uint2> work;
+    work.reserve(nunits);
+    for (size_t i = 0; i < nlists; ++i)
+        for (uint32_t u = 0; u < sv->items[i]; ++u) work.push_back(make_uint2((uint32_t)i, u));
+    // device memory of the pool's records
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = pad256(off + bytes);
+        return at;
+    };
+    const size_t o_lists = take(sizeof(ListDev) * nlists), o_work = take(sizeof(uint2) * nunits),
+                 o_ranges = take(sizeof(ulonglong2) * nunits), o_pages = take(sizeof(uint2) * npages),
+                 o_meta = take(sizeof(BlockMeta) * kBlocksPerPage * npages), o_pmeta = take(4 * kPageMetaWords * npages),
+                 o_umeta = take(8 * kUnitsPerPage * npages), o_mini = take(16 * mini_ids.size()),
+                 o_ids = take(4 * mini_ids.size()), o_ws = take(kWsHeaderBytes);
+    if (cudaMalloc(&sv->mem, std::max<size_t>(off, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ICX_ENOSPC);
+    }
+    char* base = static_cast<char*>(sv->mem);
+    sv->d.lists = reinterpret_cast<ListDev*>(base + o_lists);
+    sv->d.work = reinterpret_cast<uint2*>(base + o_work);
+    sv->d.ranges = reinterpret_cast<ulonglong2*>(base + o_ranges);
+    sv->d.pages = reinterpret_cast<uint2*>(base + o_pages);
+    sv->d.meta = reinterpret_cast<BlockMeta*>(base + o_meta);
+    sv->d.pmeta = reinterpret_cast<uint32_t*>(base + o_pmeta);
+    sv->d.umeta = reinterpret_cast<uint2*>(base + o_umeta);
+    sv->d.mini = reinterpret_cast<uint64_t*>(base + o_mini);
+    sv->d.mini_ids = reinterpret_cast<uint32_t*>(base + o_ids);
+    sv->d.ws = reinterpret_cast<WsHeader*>(base + o_ws);
+    for (size_t j = 0; j < mini_ids.size(); ++j) sv->host_lists[mini_ids[j]].index = sv->d.mini + 2 * j;
+    cudaStream_t st0 = nullptr;
+    if (cudaStreamCreateWithFlags(&st0, cudaStreamNonBlocking) != cudaSuccess) return fail(ICX_ECUDA);
+    bool ok = cudaMemset(sv->d.ws, 0, kWsHeaderBytes) == cudaSuccess;
+    if (ok && nlists)
+        ok = cudaMemcpy(sv->d.lists, sv->host_lists.data(), sizeof(ListDev) * nlists, cudaMemcpyHostToDevice) ==
+             cudaSuccess;
+    if (ok && nunits)
+        ok = cudaMemcpy(sv->d.work, work.data(), sizeof(uint2) * nunits, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && npages)
+        ok = cudaMemcpy(sv->d.pages, pages.data(), sizeof(uint2) * npages, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !mini_ids.empty()) {
+        ok = cudaMemcpy(sv->d.mini_ids, mini_ids.data(), 4 * mini_ids.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        batch_mini_index_kernel<<<(unsigned)((mini_ids.size() + 127) / 128), 128, 0, st0>>>(
+            sv->d.lists, sv->d.mini_ids, (uint32_t)mini_ids.size(), sv->d.mini, sv->d.ws);
+    }
+    // the pool's copy ranges and page records, once
+    if (ok && nunits)
+        batch_ranges_kernel<<<(unsigned)((nunits + 255) / 256), 256, 0, st0>>>(sv->d.lists, sv->d.work,
+                                                                              (uint32_t)nunits, sv->d.ranges);
+    if (ok && nlarge)
+        batch_meta_kernel<<<(unsigned)nlarge, kMetaThreads, 0, st0>>>(sv->d.lists, sv->d.pages, sv->d.meta,
+                                                                      sv->d.pmeta, sv->d.umeta, sv->d.ranges, sv->d.ws);
+    if (ok && nsmall)
+        batch_meta_small_kernel<<<(unsigned)((nsmall + kSmallWarps - 1) / kSmallWarps), kSmallWarps * 32, 0, st0>>>(
+            sv->d.lists, sv->d.pages + nlarge, (uint32_t)nsmall, sv->d.meta, sv->d.pmeta, sv->d.umeta, sv->d.ranges,
+            sv->d.ws);
+    ok = ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st0) == cudaSuccess;
+    cudaStreamDestroy(st0);
+    if (!ok) return fail(ICX_ECUDA);
+    unsigned status = 0;
+    cudaMemcpy(&status, &sv->d.ws->status, 4, cudaMemcpyDeviceToHost);
+    if (status) return fail((icx_status)status);
+    sv->unit_ranges.resize(nunits);
+    if (nunits && cudaMemcpy(sv->unit_ranges.data(), sv->d.ranges, sizeof(ulonglong2) * nunits,
+                             cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ICX_ECUDA);
+    // decode-buffer arena and per-stream state
+    if (cudaMalloc(&sv->arena, sv->budget) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ICX_ENOSPC);
+    }
+    sv->alloc.reset(sv->budget);
+    const size_t ws_bytes = pad256(kWsHeaderBytes + 32 * (kServeMaxItems / 4 + 16));
+    const size_t per_lane = ws_bytes + pad256(sizeof(ServeItem) * kServeMaxItems) + pad256(sizeof(InstDev) * kServeMaxInsts);
+    if (cudaMalloc(&sv->lane_mem, per_lane * streams) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ICX_ENOSPC);
+    }
+    if (cudaMemset(sv->lane_mem, 0, per_lane * streams) != cudaSuccess) return fail(ICX_ECUDA);
+    sv->lanes.resize(streams);
+    for (int k = 0; k < streams; ++k) {
+        auto& l = sv->lanes[k];
+        char* b = static_cast<char*>(sv->lane_mem) + per_lane * k;
+        l.ws = reinterpret_cast<WsHeader*>(b);
+        l.d_items = reinterpret_cast<ServeItem*>(b + ws_bytes);
+        l.d_insts = reinterpret_cast<InstDev*>(b + ws_bytes + pad256(sizeof(ServeItem) * kServeMaxItems));
+        if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&l.h_items, sizeof(ServeItem) * kServeMaxItems) != cudaSuccess ||
+            cudaMallocHost(&l.h_insts, sizeof(InstDev) * kServeMaxInsts) != cudaSuccess)
+            return fail(ICX_ECUDA);
+    }
+    const int smem = kBatchHdr + sv->W * kWarpBytes;
+    cudaError_t e;
+    if (sv->W == 4) {
+        e = cudaFuncSetAttribute(batch_decode_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sv->blocks, batch_decode_kernel<4, true>, 128, smem);
+    } else {
+        e = cudaFuncSetAttribute(batch_decode_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sv->blocks, batch_decode_kernel<8, true>, 256, smem);
+    }
+    if (e != cudaSuccess) return fail(ICX_ECUDA);
+    sv->blocks = std::max(sv->blocks, 1);
+    cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, sv->device);
+    *out = sv;
+    return ICX_OK;
+}
+
+icx_status icx_server_run(icx_server* sv, size_t nreq, const uint64_t* arrival_ns, const uint64_t* offs,
+                          const uint32_t* ids, uint64_t* latency_ns, uint32_t* results, const uint64_t* res_off,
+                          icx_server_stats* stats) {
+    using namespace icx;
+    using clock = std::chrono::steady_clock;
+    if (!sv || (nreq && (!arrival_ns || !offs || !ids || !latency_ns)) || (results && !res_off)) return ICX_EINVAL;
+    // per request: buffer bytes, work items, instances, integers
+    std::vector<size_t> rbytes(nreq), ritems(nreq), rints(nreq);
+    for (size_t r = 0; r < nreq; ++r) {
+        if (offs[r + 1] < offs[r] || (r && arrival_ns[r] < arrival_ns[r - 1])) return ICX_EINVAL;
+        size_t b = 0, it = 0, n = 0;
+        for (uint64_t j = offs[r]; j < offs[r + 1]; ++j) {
+            if (ids[j] >= sv->nlists) return ICX_EINVAL;
+            b += out_bytes(sv->host_lists[ids[j]].n);
+            it += sv->items[ids[j]];
+            n += sv->host_lists[ids[j]].n;
+        }
+        rbytes[r] = pad256(std::max<size_t>(b, 16));
+        ritems[r] = it;
+        rints[r] = n;
+        if (rbytes[r] > sv->budget || it > kServeMaxItems || offs[r + 1] - offs[r] > kServeMaxInsts) return ICX_ENOSPC;
+    }
+    icx_server_stats S{};
+    std::deque<uint32_t> pending;
+    size_t next = 0, done = 0;
+    const int W = sv->W;
+    const int smem = kBatchHdr + W * kWarpBytes;
+    const auto t0 = clock::now();
+    auto now_ns = [&]() { return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count(); };
+    uint64_t first_arrival = nreq ? arrival_ns[0] : 0, last_done = 0;
+    icx_status err = ICX_OK;
+    auto complete = [&](icx_server::Lane& l) {
+        const uint64_t t = now_ns();
+        for (size_t q = 0; q < l.reqs.size(); ++q) {
+            const uint32_t r = l.reqs[q];
+            latency_ns[r] = t - arrival_ns[r];
+            if (results) {
+                size_t o = l.offs[q], e = res_off[r];
+                for (uint64_t j = offs[r]; j < offs[r + 1]; ++j) {
+                    const size_t n = sv->host_lists[ids[j]].n;
+                    if (n && cudaMemcpy(results + e, sv->arena + o, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+                        err = ICX_ECUDA;
+                    o += out_bytes(n);
+                    e += n;
+                }
+            }
+            sv->alloc.release(l.offs[q], rbytes[r]);
+            S.ints += rints[r];
+        }
+        done += l.reqs.size();
+        S.requests += l.reqs.size();
+        l.reqs.clear();
+        l.offs.clear();
+        l.busy = false;
+        last_done = t;
+    };
+    auto launch = [&](icx_server::Lane& l) -> bool {
+        size_t nitems = 0, ninst = 0;
+        while (!pending.empty()) {
+            const uint32_t r = pending.front();
+            const size_t k = offs[r + 1] - offs[r];
+            if (nitems + ritems[r] > kServeMaxItems || ninst + k > kServeMaxInsts) break;
+            const size_t at = sv->alloc.alloc(rbytes[r]);
+            if (at == SIZE_MAX) break;  // wait for buffers to be freed
+            pending.pop_front();
+            l.reqs.push_back(r);
+            l.offs.push_back(at);
+            size_t o = at;
+            for (uint64_t j = offs[r]; j < offs[r + 1]; ++j) {
+                const uint32_t id = ids[j];
+                l.h_insts[ninst] = InstDev{id, 0, reinterpret_cast<uint32_t*>(sv->arena + o)};
+                const ulonglong2* rg = sv->unit_ranges.data() + sv->item_base[id];
+                for (uint32_t u = 0; u < sv->items[id]; ++u) {
+                    ServeItem& it = l.h_items[nitems++];
+                    it.src = rg[u].x;
+                    it.size = (uint32_t)rg[u].y;
+                    it.inst = (uint32_t)ninst;
+                    it.u = u;
+                }
+                ++ninst;
+                o += out_bytes(sv->host_lists[id].n);
+            }
+        }
+        if (l.reqs.empty()) return false;
+        S.batches++;
+        S.max_batch = std::max<uint64_t>(S.max_batch, l.reqs.size());
+        cudaMemcpyAsync(l.d_insts, l.h_insts, sizeof(InstDev) * ninst, cudaMemcpyHostToDevice, l.st);
+        if (nitems) {
+            cudaMemcpyAsync(l.d_items, l.h_items, sizeof(ServeItem) * nitems, cudaMemcpyHostToDevice, l.st);
+            const size_t ntiles = (nitems + W - 1) / W;
+            const int grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)sv->blocks * sv->sms, ntiles));
+            if (W == 4)
+                batch_decode_kernel<4, true><<<grid, 128, smem, l.st>>>(sv->d.lists, nullptr, (uint32_t)nitems, nullptr,
+                                                                       sv->d.meta, sv->d.pmeta, true, l.ws, l.d_items,
+                                                                       l.d_insts);
+            else
+                batch_decode_kernel<8, true><<<grid, 256, smem, l.st>>>(sv->d.lists, nullptr, (uint32_t)nitems, nullptr,
+                                                                       sv->d.meta, sv->d.pmeta, true, l.ws, l.d_items,
+                                                                       l.d_insts);
+        }
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(l.ev, l.st) != cudaSuccess) err = ICX_ECUDA;
+        l.busy = true;
+        return true;
+    };
+    while (done < nreq && err == ICX_OK) {
+        const uint64_t t = now_ns();
+        while (next < nreq && arrival_ns[next] <= t) pending.push_back((uint32_t)next++);
+        S.max_queue = std::max<uint64_t>(S.max_queue, pending.size());
+        bool progressed = false;
+        for (auto& l : sv->lanes) {
+            if (!l.busy) continue;
+            const cudaError_t q = cudaEventQuery(l.ev);
+            if (q == cudaSuccess) {
+                complete(l);
+                progressed = true;
+            } else if (q != cudaErrorNotReady) {
+                err = ICX_ECUDA;
+            }
+        }
+        for (auto& l : sv->lanes)
+            if (!l.busy && !pending.empty() && launch(l)) progressed = true;
+        if (!progressed && pending.empty() && next < nreq) {
+            bool any = false;
+            for (auto& l : sv->lanes) any |= l.busy;
+            if (!any) {
+                // idle until the next arrival (spin for the last stretch)
+                const uint64_t wait = arrival_ns[next] > t ? arrival_ns[next] - t : 0;
+                if (wait > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(wait - 100000));
+            }
+        }
+    }
+    for (auto& l : sv->lanes)
+        if (l.busy) cudaEventSynchronize(l.ev);
+    cudaDeviceSynchronize();
+    S.peak_bytes = sv->alloc.peak();
+    S.wall_s = nreq ? (double)(last_done - std::min(first_arrival, last_done)) * 1e-9 : 0.0;
+    if (stats) *stats = S;
+    if (err != ICX_OK) return err;
+    for (auto& l : sv->lanes) {
+        unsigned status = 0;
+        if (cudaMemcpy(&status, &l.ws->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return ICX_ECUDA;
+        if (status) {
+            cudaMemset(&l.ws->status, 0, 4);
+            return (icx_status)status;
+        }
+    }
+    return ICX_OK;
 }
 
 }  // extern "C"
