@@ -305,11 +305,11 @@ def run_gpu(args, world, rank, local):
     headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
 
     e2e = run_e2e(args, streams, out, ws, dev, world)
-    batched = None
+    batched = serving = None
     if not args.skip_batch:
         del out
         torch.cuda.empty_cache()
-        batched = run_batched(args, dev, flush_l2, world)
+        batched, serving = run_batched(args, dev, flush_l2, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(arrays, args)
@@ -329,6 +329,7 @@ def run_gpu(args, world, rank, local):
         "headline_kernel": kern[headline],
         "e2e": e2e,
         "batched": batched,
+        "serving": serving,
         "gpu_launches": launches_per_step * K,
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -468,7 +469,59 @@ def run_batched(args, dev, flush_l2, world):
     }
     plan.close()
     log(f"[bench] batched: {res['value']} Gints/s vs per-list {res['per_list_value']} ({res['ratio_vs_per_list']}x)")
-    return res
+    serving = None
+    if not args.skip_serve:
+        del out
+        torch.cuda.empty_cache()
+        serving = run_serving(args, pool, L)
+    return res, serving
+
+
+def run_serving(args, pool, L):
+    """Serving loop over the batch's pool, resident in HBM: Poisson arrivals
+    at each rate for args.serve_seconds; per request k ~ U{2..8} lists drawn
+    with weight rank^-1.1 (rank 1 = longest list); 16 GB of decode buffers;
+    latency = scheduled arrival -> completion event observed on the host."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+    from paper_1209_2137_gb300 import workloads as W
+
+    dummy = torch.empty(16, dtype=torch.int32, device=pool.x.device)
+    descs = pool.descs(dummy, np.zeros(len(L), dtype=np.int64))
+    sv = icx.Server(descs, budget_bytes=args.serve_budget, streams=args.serve_streams)
+    by_rank = np.argsort(-L, kind="stable")
+    w = np.arange(1, len(L) + 1, dtype=np.float64) ** -1.1
+    cum = np.cumsum(w) / w.sum()
+    rows = []
+    for i, rate in enumerate(args.serve_rates):
+        nreq = int(rate * args.serve_seconds)
+        z = W.splitmix64(W.SEED_BASE + 5, 100 * i, 3 * nreq)
+        u = ((z[:nreq] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+        arrival = np.cumsum(-np.log(u) / rate * 1e9).astype(np.uint64)
+        k = 2 + (z[nreq:2 * nreq] % np.uint64(7)).astype(np.int64)
+        offs = np.zeros(nreq + 1, dtype=np.int64)
+        np.cumsum(k, out=offs[1:])
+        zz = W.splitmix64(W.SEED_BASE + 6, 100 * i, int(offs[-1]))
+        uu = ((zz >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+        ids = by_rank[np.minimum(np.searchsorted(cum, uu), len(L) - 1)].astype(np.uint32)
+        lat, st, _ = sv.run(arrival, offs, ids)
+        ms = lat.astype(np.float64) / 1e6
+        span = float(arrival[-1]) / 1e9 if nreq else 0.0
+        rows.append({"rate_req_s": rate, "requests": nreq, "seconds": round(span, 2),
+                     "p50_ms": round(float(np.percentile(ms, 50)), 3), "p99_ms": round(float(np.percentile(ms, 99)), 3),
+                     "max_ms": round(float(ms.max()), 3),
+                     "gints_s": round(st["ints"] / max(st["wall_s"], 1e-9) / 1e9, 3),
+                     "ints_per_request": round(st["ints"] / max(1, nreq)), "batches": int(st["batches"]),
+                     "mean_batch": round(nreq / max(1, st["batches"]), 2), "max_batch": int(st["max_batch"]),
+                     "max_queue": int(st["max_queue"]), "peak_buffer_gb": round(st["peak_bytes"] / 2**30, 3)})
+        log(f"[bench] serve {rate} req/s: p50 {rows[-1]['p50_ms']} ms p99 {rows[-1]['p99_ms']} ms, "
+            f"{rows[-1]['gints_s']} Gints/s, {rows[-1]['mean_batch']} req/batch")
+    sv.close()
+    return {"workload": "the batch's pool resident in HBM; Poisson arrivals; k ~ U{2..8} lists per request, "
+                        "weight rank^-1.1 by length; FCFS admission", "budget_bytes": args.serve_budget,
+            "streams": args.serve_streams, "latency": "scheduled arrival -> completion event observed (host)",
+            "rates": rows}
 
 
 # --------------------------------------------------------- CPU baseline --
@@ -554,6 +607,11 @@ def main():
     ap.add_argument("--batch-lists", type=int, default=65536)
     ap.add_argument("--batch-total", type=int, default=1 << 28)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--skip-serve", action="store_true", help="skip the serving loop")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 10000, 100000])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-budget", type=int, default=16 << 30)
+    ap.add_argument("--serve-streams", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
