@@ -155,6 +155,12 @@ def barrier(world):
         dist.barrier()
 
 
+def aggregate_rate(ints_per_rank: int, slowest_ms: float, world: int) -> float:
+    """Whole-job G ints/s: every rank decodes ints_per_rank integers (weak
+    scaling, replicas) and the job takes as long as its slowest rank."""
+    return world * ints_per_rank / (slowest_ms / 1e3) / 1e9
+
+
 def max_over_ranks(value: float, world: int) -> float:
     if world == 1:
         return value
@@ -280,7 +286,7 @@ def run_gpu(args, world, rank, local):
     ms_per_step = float(np.mean(step_ms))
     total_ms = max_over_ranks(float(step_ms.sum()), world)
     ints_per_step = sum(s["n"] for s in streams)
-    value = world * ints_per_step * K / (total_ms / 1e3) / 1e9
+    value = aggregate_rate(ints_per_step * K, total_ms, world)
     launches_per_step = sum(1 if s["codec"] == "bp128" else 2 for s in streams)
     ws.raise_status("timed decodes")
 
