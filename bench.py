@@ -215,6 +215,7 @@ def run_gpu(args, world, rank, local):
         icx.set_tuning("bp128.warps_per_cta", args.bp128_warps)
     if args.bp128_l2_prefetch >= 0:
         icx.set_tuning("bp128.l2_prefetch", args.bp128_l2_prefetch)
+
     arrays = workload_arrays(args.n)
     stream = torch.cuda.current_stream()
 
