@@ -60,7 +60,7 @@ struct WarpCtx {
     uint32_t valid, list, pad[4];
 };
 static_assert(sizeof(WarpCtx) == 112, "warp context");
-constexpr int kWarpBytes = kBatchBuf + 16 * 16 + 2048 + (int)sizeof(WarpCtx);
+constexpr int kWarpBytes = kBatchBuf + 16 * 16 + 2048 + (int)sizeof(WarpCtx) + 128;
 static_assert(kWarpBytes % 16 == 0, "warp region");
 
 struct BatchShared {
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     BlockMeta* m = reinterpret_cast<BlockMeta*>(wbase + kBatchBuf);
     uint8_t* blk_of = wbase + kBatchBuf + 256;
     WarpCtx& C = *reinterpret_cast<WarpCtx*>(wbase + kBatchBuf + 256 + 2048);
+    uint32_t* pg = reinterpret_cast<uint32_t*>(wbase + kBatchBuf + 256 + 2048 + sizeof(WarpCtx));  // array offsets
     const uint32_t ntiles = (nwork + W - 1) / W;
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             if ((uint32_t)lane < K)
                 reinterpret_cast<uint4*>(m)[lane] =
                     reinterpret_cast<const uint4*>(meta + (size_t)kBlocksPerPage * slot + 16 * q)[lane];
+            pg[lane] = pmeta[(size_t)kPageMetaWords * slot + lane];
             if (lane == 0) {
                 C.slot = slot;
                 C.pbase = C.L.index[p];
@@ -349,8 +351,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             if (lane == 0 && pf.y && pf.y != ~0ull) prefetch_l2(reinterpret_cast<const void*>(pf.x), (uint32_t)pf.y);
             if (ok) {
                 if (codec == ICX_CODEC_FASTPFOR) {
-                    fp_unit_unpack_patch(C.L.in, C.pbase, pmeta + (size_t)kPageMetaWords * C.slot, m, K, buf, blk_of,
-                                         v, h, lane);
+                    fp_unit_unpack_patch(C.L.in, C.pbase, pg, m, K, buf, blk_of, v, h, lane);
                 } else if (fmt == ICX_FMT_W32) {
                     ok = bp128_unpack_unit<ICX_FMT_W32>(buf, size, K, v, h, lane);
                     residue = ok;

@@ -90,6 +90,7 @@ struct FpSmem {
     TileShared t;
     uint64_t bar[kWarps];
     BlockMeta m[kWarps][16];
+    uint32_t pg[kWarps][32];           // the unit's page: offsets of its exception arrays
     uint8_t blk_of[kWarps][16 * 128];  // block of the unit's q-th exception
 };
 
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         uint2 um;
         uint32_t bad;
         uint4 mrec;
+        uint32_t arr;  // lane l: offset of exception array l + 1
     };
     auto prefetch = [&](uint32_t t, Rec& r) {
         const uint32_t uu = t * kWarps + warp;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 r.bad = pmeta[kPageMetaWords * p + 32];
             }
             if ((uint32_t)lane < K) r.mrec = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
+            r.arr = pmeta[kPageMetaWords * p + lane];
         }
     };
     // publishes the records and starts the bulk copy; returns 0 = nothing to
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         const uint32_t uu = t * kWarps + warp;
         if (t < ntiles && uu < U) {
             if (lane < 16) reinterpret_cast<uint4*>(m)[lane] = r.mrec;
+            S.pg[warp][lane] = r.arr;
             __syncwarp();
             if (lane == 0) {
                 if (r.bad) {
@@ -172,9 +176,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
         uint32_t K = 0;
+        // the page whose first unit is one grid of tiles ahead: into L2 now
+        // (packed bits, byte array and exception arrays), so the copies and
+        // exception gathers of its units hit L2
+        const uint32_t ahead = u + gridDim.x * kWarps;
+        uint64_t pf_a = 0, pf_b = 0;
+        if (lane == 0 && ahead < U && ahead % kUnitsPerPage == 0) {
+            pf_a = __ldg(index + ahead / kUnitsPerPage);
+            pf_b = __ldg(index + ahead / kUnitsPerPage + 1);
+        }
         if (u < U) {
             K = (uint32_t)min((size_t)16, nb - 16 * (size_t)u);
-            const uint32_t* pg = pmeta + kPageMetaWords * (u / kUnitsPerPage);
+            const uint32_t* pg = S.pg[warp];  // staged with the block records
             Rec r{};
             prefetch(tile, r);
             const uint64_t pbase = __shfl_sync(FULL, r.pbase, 0);
@@ -187,6 +200,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 phase ^= 1;
                 if (!ok && lane == 0) set_error(h, ICX_ETIMEOUT);
             }
+            if (lane == 0 && pf_a < pf_b && pf_b <= in_bytes && ((pf_a | pf_b) & 15) == 0)
+                prefetch_l2(in + pf_a, (uint32_t)min(pf_b - pf_a, (uint64_t)0x7FFFFFF0u));
             if (ok) fp_unit_unpack_patch(in, pbase, pg, m, K, buf, blk_of, v, h, lane);
         } else if (u == U) {
             const uint32_t count = (uint32_t)(n - 128 * nb);
