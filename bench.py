@@ -312,6 +312,7 @@ def run_gpu(args, world, rank, local):
     headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
 
     e2e = run_e2e(args, streams, out, ws, dev, world)
+    exceptions = None if args.skip_exceptions else run_exceptions(args, out, ws, flush_l2, world)
     batched = serving = None
     if not args.skip_batch:
         del out
@@ -335,6 +336,7 @@ def run_gpu(args, world, rank, local):
         "roofline": roofline,
         "headline_kernel": kern[headline],
         "e2e": e2e,
+        "exceptions": exceptions,
         "batched": batched,
         "serving": serving,
         "gpu_launches": launches_per_step * K,
@@ -399,6 +401,49 @@ def run_e2e(args, streams, out, ws, dev, world):
     ints = sum(s["n"] for s in streams) * steps * world
     return {"value": round(ints / (ms / 1e3) / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+# ------------------------------------------------- exception-heavy data --
+
+def run_exceptions(args, out, ws, flush_l2, world):
+    """2^26 unsorted integers, 90 % geometric (mean 8), 10 % uniform in
+    [2^20, 2^28): SIMD-FastPFOR without differential decoding (unpack plus
+    exception patch), and SIMD-BP128 on the same data for contrast."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+    from paper_1209_2137_gb300 import workloads as W
+
+    x = W.workload_exceptions()
+    xt = torch.from_numpy(x).to(out.device)
+    o = out[: x.size]
+    peak, _ = peaks()
+    res = {"workload": f"{x.size} unsorted uint32: 90 % geometric (mean 8), 10 % uniform in [2^20, 2^28)"}
+    for codec, label in (("fastpfor", "SIMD-FastPFOR"), ("bp128", "SIMD-BP128")):
+        enc = icx.fastpfor_encode(xt, icx.DELTA_NONE) if codec == "fastpfor" else icx.bp128_encode(xt, icx.DELTA_NONE)
+        icx.decode(enc, out=o, workspace=ws)
+        ws.raise_status("exception-heavy decode")
+        if not torch.equal(o, xt):
+            raise SystemExit(f"exception-heavy {label}: verification failed")
+        for _ in range(args.warmup):
+            flush_l2()
+            icx.decode(enc, out=o, workspace=ws)
+        steps = max(3, min(args.steps, 50))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush_l2()
+            a.record()
+            icx.decode(enc, out=o, workspace=ws)
+            b.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world)
+        alg = enc.nbytes + 8 * enc.index.numel() + 4 * x.size
+        res[label] = {"bits_per_int": round(8.0 * enc.nbytes / x.size, 3), "ms": round(ms, 4),
+                      "gints_s": round(x.size / (ms / 1e3) / 1e9, 1),
+                      "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
+    res["note"] = "the GPU encoders write the oracle's bytes (tests), so bits_per_int is the oracle's"
+    log(f"[bench] exception-heavy: SIMD-FastPFOR {res['SIMD-FastPFOR']}, SIMD-BP128 {res['SIMD-BP128']}")
+    return res
 
 
 # ------------------------------------------------------- batched decode --
@@ -610,6 +655,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
     ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
+    ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
     ap.add_argument("--batch-lists", type=int, default=65536)
     ap.add_argument("--batch-total", type=int, default=1 << 28)

@@ -216,8 +216,10 @@ static_assert(sizeof(ServeItem) == 32, "serve item");
 
 // SERVE = false: work items are (list, unit) of a plan with per-item copy
 // ranges; SERVE = true: serving-loop items (ServeItem) whose instances
-// (InstDev) name the list and the output, segments are instances.
-template <int W, bool SERVE>
+// (InstDev) name the list and the output, segments are instances.  CODEC:
+// -1 = items of both codecs, else only that codec's (the other code path is
+// compiled out).
+template <int W, bool SERVE, int CODEC = -1>
 __global__ void __launch_bounds__(W * 32, 16 / W)
     batch_decode_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ work, uint32_t nwork,
                         const ulonglong2* __restrict__ ranges, const BlockMeta* __restrict__ meta,
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         const uint32_t u = C.u, M = C.L.units;
         const uint64_t nb = C.L.n / 128;
         const uint32_t K = u < M ? (uint32_t)min((uint64_t)16, nb - 16 * (uint64_t)u) : 0u;
-        if (u < M && C.L.codec == ICX_CODEC_FASTPFOR) {
+        if (CODEC != ICX_CODEC_BP128 && u < M && (CODEC == ICX_CODEC_FASTPFOR || C.L.codec == ICX_CODEC_FASTPFOR)) {
             const uint32_t p = u / kUnitsPerPage, q = u % kUnitsPerPage;
             const uint32_t slot = C.L.page_slot + p;
             if ((uint32_t)lane < K)
@@ -350,12 +352,13 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             }
             if (lane == 0 && pf.y && pf.y != ~0ull) prefetch_l2(reinterpret_cast<const void*>(pf.x), (uint32_t)pf.y);
             if (ok) {
-                if (codec == ICX_CODEC_FASTPFOR) {
+                const bool fp = CODEC == ICX_CODEC_FASTPFOR || (CODEC == -1 && codec == ICX_CODEC_FASTPFOR);
+                if (CODEC != ICX_CODEC_BP128 && fp) {
                     fp_unit_unpack_patch(C.L.in, C.pbase, pg, m, K, buf, blk_of, v, h, lane);
-                } else if (fmt == ICX_FMT_W32) {
+                } else if (CODEC != ICX_CODEC_FASTPFOR && fmt == ICX_FMT_W32) {
                     ok = bp128_unpack_unit<ICX_FMT_W32>(buf, size, K, v, h, lane);
                     residue = ok;
-                } else {
+                } else if (CODEC != ICX_CODEC_FASTPFOR) {
                     bp128_unpack_unit<ICX_FMT_PAPER>(buf, size, K, v, h, lane);
                 }
             }
@@ -459,9 +462,11 @@ struct PlanMem {
     uint2* umeta = nullptr;
     uint64_t* mini = nullptr;
     uint32_t* mini_ids = nullptr;
-    WsHeader* ws = nullptr;
+    WsHeader* ws = nullptr;   // page parses and SIMD-FastPFOR items
+    WsHeader* ws2 = nullptr;  // SIMD-BP128 items
 };
 
+template <int CODEC>
 static cudaError_t batch_occupancy(int W, int* blocks, int* sms) {
     const int smem = kBatchHdr + W * kWarpBytes;
     cudaError_t e;
@@ -469,16 +474,32 @@ static cudaError_t batch_occupancy(int W, int* blocks, int* sms) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
     if (W == 4) {
-        e = cudaFuncSetAttribute(batch_decode_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(batch_decode_kernel<4, false, CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<4, false>, W * 32, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<4, false, CODEC>, W * 32,
+                                                              smem);
     } else {
-        e = cudaFuncSetAttribute(batch_decode_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(batch_decode_kernel<8, false, CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<8, false>, W * 32, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_decode_kernel<8, false, CODEC>, W * 32,
+                                                              smem);
     }
     if (*blocks < 1) *blocks = 1;
     return e;
+}
+
+template <int CODEC>
+static void launch_batch(int W, int grid, cudaStream_t st, const PlanMem& d, const uint2* work, uint32_t nwork,
+                         const ulonglong2* ranges, bool l2, WsHeader* ws) {
+    const int smem = kBatchHdr + W * kWarpBytes;
+    if (W == 4)
+        batch_decode_kernel<4, false, CODEC><<<grid, 128, smem, st>>>(d.lists, work, nwork, ranges, d.meta, d.pmeta,
+                                                                     l2, ws);
+    else
+        batch_decode_kernel<8, false, CODEC><<<grid, 256, smem, st>>>(d.lists, work, nwork, ranges, d.meta, d.pmeta,
+                                                                     l2, ws);
 }
 
 }  // namespace icx
@@ -490,14 +511,15 @@ struct icx_plan {
     std::vector<icx_list_desc> lists;
     std::vector<ListDev> host_lists;
     std::vector<uint32_t> items_per_list;  // work items of each list
-    size_t nwork = 0, npages = 0, nlarge = 0, nsmall = 0, nmini = 0;
+    size_t nwork = 0, nwork_bp = 0, npages = 0, nlarge = 0, nsmall = 0, nmini = 0;
     size_t max_n = 0;
     void* mem = nullptr;
     icx::PlanMem d;
     icx_tuning tune{8, 0, 1, nullptr};
     cudaStream_t cap = nullptr;   // capture stream
     cudaStream_t cap2 = nullptr;  // second branch of the graph (small pages)
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t cap3 = nullptr;  // third branch (SIMD-BP128 items)
+    cudaEvent_t fork = nullptr, join = nullptr, join3 = nullptr;
     cudaGraphExec_t exec = nullptr;
     // per-list baseline
     void* single_ws = nullptr;
@@ -571,10 +593,13 @@ std::vector<uint2> build_work(const icx_plan& p, int order) {
     else if (order == 2)
         std::stable_sort(ids.begin(), ids.end(),
                          [&](uint32_t a, uint32_t b) { return p.items_per_list[a] < p.items_per_list[b]; });
+    // SIMD-BP128 lists first, then SIMD-FastPFOR lists (one decode kernel each)
     std::vector<uint2> w;
     w.reserve(p.nwork);
-    for (uint32_t id : ids)
-        for (uint32_t u = 0; u < p.items_per_list[id]; ++u) w.push_back(make_uint2(id, u));
+    for (int codec : {ICX_CODEC_BP128, ICX_CODEC_FASTPFOR})
+        for (uint32_t id : ids)
+            if (p.lists[id].codec == codec)
+                for (uint32_t u = 0; u < p.items_per_list[id]; ++u) w.push_back(make_uint2(id, u));
     return w;
 }
 
@@ -585,18 +610,29 @@ cudaError_t capture(icx_plan* p) {
         p->exec = nullptr;
     }
     const int W = p->tune.warps_per_cta;
-    const int smem = kBatchHdr + W * kWarpBytes;
-    int blocks = 1, sms = 1;
-    cudaError_t e = batch_occupancy(W, &blocks, &sms);
+    const bool l2 = p->tune.l2_prefetch != 0;
+    int b_bp = 1, b_fp = 1, sms = 1;
+    cudaError_t e = batch_occupancy<ICX_CODEC_BP128>(W, &b_bp, &sms);
+    if (e == cudaSuccess) e = batch_occupancy<ICX_CODEC_FASTPFOR>(W, &b_fp, &sms);
     if (e != cudaSuccess) return e;
-    const size_t ntiles = (p->nwork + W - 1) / W;
-    const int grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)blocks * sms, ntiles));
+    // both decode kernels are persistent over their work-lists with a full
+    // grid each: the second one's CTAs take the SMs as the first one's finish
+    const size_t n_bp = p->nwork_bp, n_fp = p->nwork - p->nwork_bp;
+    const size_t g_bp = std::min<size_t>((size_t)b_bp * sms, (n_bp + W - 1) / W);
+    const size_t g_fp = std::min<size_t>((size_t)b_fp * sms, (n_fp + W - 1) / W);
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    // the two page parses run side by side (fork / join inside the graph)
+    cudaEventRecord(p->fork, p->cap);
+    // branch 3: SIMD-BP128 items (no page parse needed)
+    if (n_bp) {
+        cudaStreamWaitEvent(p->cap3, p->fork, 0);
+        launch_batch<ICX_CODEC_BP128>(W, (int)g_bp, p->cap3, p->d, p->d.work, (uint32_t)n_bp, p->d.ranges, l2,
+                                      p->d.ws2);
+        cudaEventRecord(p->join3, p->cap3);
+    }
+    // branch 2: short pages; main: long pages, then SIMD-FastPFOR items
     if (p->nsmall) {
-        cudaEventRecord(p->fork, p->cap);
         cudaStreamWaitEvent(p->cap2, p->fork, 0);
         batch_meta_small_kernel<<<(unsigned)((p->nsmall + kSmallWarps - 1) / kSmallWarps), kSmallWarps * 32, 0,
                                   p->cap2>>>(p->d.lists, p->d.pages + p->nlarge, (uint32_t)p->nsmall, p->d.meta,
@@ -608,16 +644,10 @@ cudaError_t capture(icx_plan* p) {
                                                                            p->d.pmeta, p->d.umeta, p->d.ranges,
                                                                            p->d.ws);
     if (p->nsmall) cudaStreamWaitEvent(p->cap, p->join, 0);
-    if (p->nwork) {
-        if (W == 4)
-            batch_decode_kernel<4, false><<<grid, 4 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
-                                                                   p->d.ranges, p->d.meta, p->d.pmeta,
-                                                                   p->tune.l2_prefetch != 0, p->d.ws);
-        else
-            batch_decode_kernel<8, false><<<grid, 8 * 32, smem, p->cap>>>(p->d.lists, p->d.work, (uint32_t)p->nwork,
-                                                                   p->d.ranges, p->d.meta, p->d.pmeta,
-                                                                   p->tune.l2_prefetch != 0, p->d.ws);
-    }
+    if (n_fp)
+        launch_batch<ICX_CODEC_FASTPFOR>(W, (int)g_fp, p->cap, p->d, p->d.work + n_bp, (uint32_t)n_fp,
+                                         p->d.ranges + n_bp, l2, p->d.ws);
+    if (n_bp) cudaStreamWaitEvent(p->cap, p->join3, 0);
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(p->cap, &g);
     if (le != cudaSuccess) e = le;
@@ -787,6 +817,7 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
         p->items_per_list[i] = layout_list(lists[i], (uint32_t)i, p->host_lists[i], p->npages, pages, small_pages,
                                            mini_ids);
         p->nwork += p->items_per_list[i];
+        if (lists[i].codec == ICX_CODEC_BP128) p->nwork_bp += p->items_per_list[i];
         p->max_n = std::max(p->max_n, lists[i].n);
     }
     p->nlarge = pages.size();
@@ -810,7 +841,8 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
                  o_meta = take(sizeof(BlockMeta) * kBlocksPerPage * p->npages),
                  o_pmeta = take(4 * kPageMetaWords * p->npages), o_umeta = take(8 * kUnitsPerPage * p->npages),
                  o_mini = take(16 * p->nmini), o_ids = take(4 * p->nmini),
-                 o_ws = take(kWsHeaderBytes + 32 * (ntiles_max + 16));
+                 o_ws = take(kWsHeaderBytes + 32 * (ntiles_max + 16)),
+                 o_ws2 = take(kWsHeaderBytes + 32 * (ntiles_max + 16));
     if (cudaMalloc(&p->mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -827,6 +859,7 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
     p->d.mini = reinterpret_cast<uint64_t*>(base + o_mini);
     p->d.mini_ids = reinterpret_cast<uint32_t*>(base + o_ids);
     p->d.ws = reinterpret_cast<WsHeader*>(base + o_ws);
+    p->d.ws2 = reinterpret_cast<WsHeader*>(base + o_ws2);
     for (size_t j = 0; j < p->nmini; ++j) p->host_lists[mini_ids[j]].index = p->d.mini + 2 * j;
     auto fail = [&](icx_status st) {
         icx_plan_destroy(p);
@@ -834,6 +867,8 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
     };
     if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join3, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(ICX_ECUDA);
@@ -843,7 +878,9 @@ icx_status icx_plan_create(const icx_list_desc* lists, size_t nlists, const icx_
     if (!pages.empty() &&
         cudaMemcpy(p->d.pages, pages.data(), sizeof(uint2) * pages.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(ICX_ECUDA);
-    if (cudaMemset(p->d.ws, 0, kWsHeaderBytes + 32 * (ntiles_max + 16)) != cudaSuccess) return fail(ICX_ECUDA);
+    if (cudaMemset(p->d.ws, 0, kWsHeaderBytes + 32 * (ntiles_max + 16)) != cudaSuccess ||
+        cudaMemset(p->d.ws2, 0, kWsHeaderBytes + 32 * (ntiles_max + 16)) != cudaSuccess)
+        return fail(ICX_ECUDA);
     if (p->nmini) {
         if (cudaMemcpy(p->d.mini_ids, mini_ids.data(), 4 * p->nmini, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(ICX_ECUDA);
@@ -950,10 +987,13 @@ icx_status icx_plan_status(icx_plan* p, icx_stream_t stream, icx_status* out) {
     using namespace icx;
     if (!p || !out) return ICX_EINVAL;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return ICX_ECUDA;
-    unsigned a = 0, b = 0;
+    unsigned a = 0, b = 0, c = 0;
     const size_t at = offsetof(WsHeader, status);
-    if (cudaMemcpy(&a, reinterpret_cast<char*>(p->d.ws) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(&a, reinterpret_cast<char*>(p->d.ws) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&c, reinterpret_cast<char*>(p->d.ws2) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return ICX_ECUDA;
+    if (!a) a = c;
+    cudaMemset(reinterpret_cast<char*>(p->d.ws2) + at, 0, 4);
     if (p->single_ws &&
         cudaMemcpy(&b, static_cast<char*>(p->single_ws) + at, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return ICX_ECUDA;
@@ -979,8 +1019,10 @@ void icx_plan_destroy(icx_plan* p) {
         cudaStreamDestroy(p->cap);
     }
     if (p->cap2) cudaStreamDestroy(p->cap2);
+    if (p->cap3) cudaStreamDestroy(p->cap3);
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
+    if (p->join3) cudaEventDestroy(p->join3);
     if (p->mem) cudaFree(p->mem);
     if (p->single_ws) cudaFree(p->single_ws);
     delete p;
