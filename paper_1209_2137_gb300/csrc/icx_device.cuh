@@ -198,18 +198,6 @@ __device__ __forceinline__ uint4 warp_incl_scan4(uint4 v, int lane) {
     return v;
 }
 
-// Row ownership: lane t holds integers 4t..4t+3 of a 128-integer block.
-// Stride-1 prefix sum of the block plus the running carry (lane-uniform).
-__device__ __forceinline__ uint4 row_scan_d1(uint4 v, uint32_t& carry, int lane) {
-    v.y += v.x;
-    v.z += v.y;
-    v.w += v.z;
-    const uint32_t incl = warp_incl_scan(v.w, lane);
-    const uint32_t add = carry + incl - v.w;
-    carry += __shfl_sync(FULL, incl, 31);
-    return make_uint4(v.x + add, v.y + add, v.z + add, v.w + add);
-}
-
 // Row ownership, stride-4 prefix sum: component c of every lane belongs to
 // residue c, so the block is four column scans over the lanes.
 __device__ __forceinline__ uint4 row_scan_d4(uint4 v, uint4& carry, int lane) {
@@ -217,24 +205,6 @@ __device__ __forceinline__ uint4 row_scan_d4(uint4 v, uint4& carry, int lane) {
     const uint4 out = add4(incl, carry);
     carry = add4(carry, shfl4(incl, 31));
     return out;
-}
-
-// Residue ownership: lane j = 4g + l holds integers 16g + 4m + l (m = 0..3)
-// in components m.  Stride-4 prefix sum: each residue l is a chain running
-// through m, then through the groups g; `carry` is the residue-l carry.
-__device__ __forceinline__ uint4 residue_scan_d4(uint4 v, uint32_t& carry, int lane) {
-    v.y += v.x;
-    v.z += v.y;
-    v.w += v.z;
-    uint32_t incl = v.w;
-#pragma unroll
-    for (int off = 4; off < 32; off <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, incl, off);
-        if (lane >= off) incl += y;
-    }
-    const uint32_t add = carry + incl - v.w;
-    carry += __shfl_sync(FULL, incl, 28 + (lane & 3));
-    return make_uint4(v.x + add, v.y + add, v.z + add, v.w + add);
 }
 
 // Residue ownership -> row ownership: inside each group of four lanes the

@@ -260,25 +260,6 @@ __device__ __forceinline__ void store_unit(uint32_t* __restrict__ out, size_t fi
     }
 }
 
-// Exclusive prefix of a unit decoded by one warp on its own: one decoupled
-// look-back per unit (no CTA barrier), stride-1 carries splatted to 4 lanes.
-template <int DELTA>
-__device__ __forceinline__ uint4 warp_unit_prefix(uint4 agg, uint32_t unit, uint32_t epoch, WsHeader* h) {
-    if (DELTA == ICX_DELTA_NONE) return make_uint4(0, 0, 0, 0);
-    if (DELTA == ICX_DELTA_1) {
-        const uint4 b = lookback<1>(h, epoch, unit, agg);
-        return make_uint4(b.x, b.x, b.x, b.x);
-    }
-    return lookback<4>(h, epoch, unit, agg);
-}
-
-// Next unit id for a warp (lane 0 takes it from the launch's counter).
-__device__ __forceinline__ uint32_t warp_grab(WsHeader* h) {
-    uint32_t u = 0;
-    if ((threadIdx.x & 31) == 0) u = atomicAdd(&h->tile_counter, 1u);
-    return __shfl_sync(FULL, u, 0);
-}
-
 // Grabs the next tile id for the CTA (thread 0), broadcast through S.tile.
 __device__ __forceinline__ uint32_t next_tile(TileShared& S, WsHeader* h) {
     if (threadIdx.x == 0) S.tile = atomicAdd(&h->tile_counter, 1u);
