@@ -215,6 +215,8 @@ def run_gpu(args, world, rank, local):
         icx.set_tuning("bp128.warps_per_cta", args.bp128_warps)
     if args.bp128_l2_prefetch >= 0:
         icx.set_tuning("bp128.l2_prefetch", args.bp128_l2_prefetch)
+    if args.fastpfor_warps:
+        icx.set_tuning("fastpfor.warps_per_cta", args.fastpfor_warps)
 
     arrays = workload_arrays(args.n)
     stream = torch.cuda.current_stream()
@@ -655,6 +657,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
     ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
+    ap.add_argument("--fastpfor-warps", type=int, default=0, help="warps per CTA of the SIMD-FastPFOR decoder")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
     ap.add_argument("--batch-lists", type=int, default=65536)

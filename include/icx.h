@@ -197,9 +197,14 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, uint8
                            icx_stream_t stream);
 
 /* Sets a launch parameter of the decoders (not part of the method):
- * "bp128.warps_per_cta" = 4, 8 or 16 warps per CTA tile of the SIMD-BP128 /
- * W32 decoder (0 = default: 4 for stride-4 deltas, 8 otherwise).  Takes effect for later launches; not thread
- * safe against concurrent launches.  ICX_EINVAL for an unknown key. */
+ *   "bp128.warps_per_cta" = 4, 8 or 16 warps per CTA tile of the SIMD-BP128 /
+ *       W32 decoder (0 = default: 4 for the paper layout, 8 for W32);
+ *   "bp128.l2_prefetch" = 1 (default) / 0: each warp prefetches into L2 the
+ *       metablock one grid of tiles ahead;
+ *   "fastpfor.warps_per_cta" = 4 or 8 warps per CTA tile of the
+ *       SIMD-FastPFOR decoder (0 = default).
+ * Takes effect for later launches; not thread safe against concurrent
+ * launches.  ICX_EINVAL for an unknown key. */
 icx_status icx_set_tuning(const char *key, int value);
 
 /* Library version string. */

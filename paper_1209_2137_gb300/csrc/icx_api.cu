@@ -187,6 +187,10 @@ icx_status icx_set_tuning(const char* key, int value) {
         icx::set_bp128_warps(value);
         return ICX_OK;
     }
+    if (!strcmp(key, "fastpfor.warps_per_cta")) {
+        icx::set_fastpfor_warps(value);
+        return ICX_OK;
+    }
     if (!strcmp(key, "bp128.l2_prefetch")) {
         icx::set_bp128_prefetch(value);
         return ICX_OK;

@@ -60,7 +60,7 @@ struct WarpCtx {
     uint32_t valid, list, pad[4];
 };
 static_assert(sizeof(WarpCtx) == 112, "warp context");
-constexpr int kWarpBytes = kBatchBuf + 16 * 16 + 2048 + (int)sizeof(WarpCtx) + 128;
+constexpr int kWarpBytes = kBatchBuf + 16 * 16 + kExScratchBytes + (int)sizeof(WarpCtx) + 128;
 static_assert(kWarpBytes % 16 == 0, "warp region");
 
 struct BatchShared {
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     uint8_t* buf = wbase;
     BlockMeta* m = reinterpret_cast<BlockMeta*>(wbase + kBatchBuf);
     uint8_t* blk_of = wbase + kBatchBuf + 256;
-    WarpCtx& C = *reinterpret_cast<WarpCtx*>(wbase + kBatchBuf + 256 + 2048);
-    uint32_t* pg = reinterpret_cast<uint32_t*>(wbase + kBatchBuf + 256 + 2048 + sizeof(WarpCtx));  // array offsets
+    WarpCtx& C = *reinterpret_cast<WarpCtx*>(wbase + kBatchBuf + 256 + kExScratchBytes);
+    uint32_t* pg = reinterpret_cast<uint32_t*>(wbase + kBatchBuf + 256 + kExScratchBytes + sizeof(WarpCtx));  // array offsets
     const uint32_t ntiles = (nwork + W - 1) / W;
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);

@@ -269,7 +269,9 @@ static cudaError_t launch_bp128_w(const uint8_t* in, size_t in_bytes, uint32_t* 
                                   const uint64_t* index, WsHeader* h, cudaStream_t s) {
     // measured on the 2^26 sorted workload: 4 warps per CTA suit the stride-4
     // scan (more CTAs per SM), 8 the others
-    const int w = g_bp128_warps ? g_bp128_warps : (DELTA == ICX_DELTA_4 ? 4 : 8);
+    // measured on the 2^26 sorted workloads: 4 warps per CTA for the paper
+    // layout, 8 for W32
+    const int w = g_bp128_warps ? g_bp128_warps : (FMT == ICX_FMT_PAPER ? 4 : 8);
     if (w == 4) return launch_bp128<DELTA, FMT, 4>(in, in_bytes, out, n, index, h, s);
     if (w == 16) return launch_bp128<DELTA, FMT, 16>(in, in_bytes, out, n, index, h, s);
     return launch_bp128<DELTA, FMT, 8>(in, in_bytes, out, n, index, h, s);

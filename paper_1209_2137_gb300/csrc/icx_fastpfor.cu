@@ -86,26 +86,27 @@ __global__ void __launch_bounds__(kMetaThreads)
 // ---------------------------------------------------------------- decode
 
 
+template <int W>
 struct FpSmem {
     TileShared t;
-    uint64_t bar[kWarps];
-    BlockMeta m[kWarps][16];
-    uint32_t pg[kWarps][32];           // the unit's page: offsets of its exception arrays
-    uint8_t blk_of[kWarps][16 * 128];  // block of the unit's q-th exception
+    uint64_t bar[W];
+    BlockMeta m[W][16];
+    uint32_t pg[W][32];           // the unit's page: offsets of its exception arrays
+    uint8_t blk_of[W][kExScratchBytes];  // block of the unit's q-th exception, then its counts
 };
 
-// A CTA of kWarps warps takes tiles of kWarps consecutive units of 16 blocks
+// A CTA of W warps takes tiles of W consecutive units of 16 blocks
 // (then the Variable Byte tail), one look-back per tile, exactly like the
 // SIMD-BP128 decoder: per warp its unit's block records, one bulk copy of
 // its packed low bits, unpack, exception patch, local scan.
-template <int DELTA>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+template <int DELTA, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
     fastpfor_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
                            const uint64_t* __restrict__ index, const BlockMeta* __restrict__ meta,
                            const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, WsHeader* h) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    FpSmem& S = *reinterpret_cast<FpSmem*>(smem_raw);
-    uint8_t* bufs = smem_raw + ((sizeof(FpSmem) + 127) / 128) * 128;
+    FpSmem<W>& S = *reinterpret_cast<FpSmem<W>*>(smem_raw);
+    uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W>) + 127) / 128) * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* buf = bufs + (size_t)warp * kFBuf;
     uint32_t* buf32 = reinterpret_cast<uint32_t*>(buf);
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     const size_t nb = n / 128;
     const uint32_t U = (uint32_t)((nb + 15) / 16);  // units of 16 blocks
     const uint32_t P = (uint32_t)((nb + kBlocksPerPage - 1) / kBlocksPerPage);
-    const uint32_t ntiles = (U + 1 + kWarps - 1) / kWarps;  // then the Variable Byte tail
+    const uint32_t ntiles = (U + 1 + W - 1) / W;  // then the Variable Byte tail
     const uint32_t epoch = launch_epoch(h);
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         uint32_t arr;  // lane l: offset of exception array l + 1
     };
     auto prefetch = [&](uint32_t t, Rec& r) {
-        const uint32_t uu = t * kWarps + warp;
+        const uint32_t uu = t * W + warp;
         if (t < ntiles && uu < U) {
             const uint32_t p = uu / kUnitsPerPage;
             const uint32_t K = (uint32_t)min((size_t)16, nb - 16 * (size_t)uu);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     // wait for, 1 = copy in flight, 2 = bad page
     auto issue = [&](uint32_t t, const Rec& r) -> uint32_t {
         uint32_t res = 0;
-        const uint32_t uu = t * kWarps + warp;
+        const uint32_t uu = t * W + warp;
         if (t < ntiles && uu < U) {
             if (lane < 16) reinterpret_cast<uint4*>(m)[lane] = r.mrec;
             S.pg[warp][lane] = r.arr;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     for (;;) {
         const uint32_t tile = next_tile(S.t, h);
         if (tile >= ntiles) break;
-        const uint32_t u = tile * kWarps + warp;
+        const uint32_t u = tile * W + warp;
         uint4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = make_uint4(0, 0, 0, 0);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         // the page whose first unit is one grid of tiles ahead: into L2 now
         // (packed bits, byte array and exception arrays), so the copies and
         // exception gathers of its units hit L2
-        const uint32_t ahead = u + gridDim.x * kWarps;
+        const uint32_t ahead = u + gridDim.x * W;
         uint64_t pf_a = 0, pf_b = 0;
         if (lane == 0 && ahead < U && ahead % kUnitsPerPage == 0) {
             pf_a = __ldg(index + ahead / kUnitsPerPage);
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             agg = unit_scan_d4_smem(v, buf32, lane);
         else
             agg = unit_local_scan<DELTA>(v, K, false, lane);
-        const uint4 pref = tile_prefix<DELTA>(S.t, agg, tile, epoch, h, warp, lane);
+        const uint4 pref = tile_prefix<DELTA, W>(S.t, agg, tile, epoch, h, warp, lane);
         if (u <= U) store_unit(out, u < U ? 2048 * (size_t)u : 128 * nb, n, v, K, pref, lane);
         if (DELTA == ICX_DELTA_NONE) __syncthreads();
     }
@@ -231,11 +232,11 @@ cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, 
     return cudaGetLastError();
 }
 
-template <int DELTA>
+template <int DELTA, int W>
 static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
                              WsHeader* h, cudaStream_t s) {
-    auto kern = fastpfor_decode_kernel<DELTA>;
-    const int smem = (int)(((sizeof(FpSmem) + 127) / 128) * 128 + (size_t)kWarps * kFBuf);
+    auto kern = fastpfor_decode_kernel<DELTA, W>;
+    const int smem = (int)(((sizeof(FpSmem<W>) + 127) / 128) * 128 + (size_t)W * kFBuf);
     static int blocks_per_sm = -1;
     static int sms = 0;
     if (blocks_per_sm < 0) {
@@ -244,7 +245,7 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kWarps * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, W * 32, smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -256,17 +257,29 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
     if (P > 0) {
         fastpfor_meta_kernel<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
     }
-    const size_t ntiles = (U + 1 + kWarps - 1) / kWarps;
+    const size_t ntiles = (U + 1 + W - 1) / W;
     const int grid = (int)min((size_t)blocks_per_sm * sms, ntiles);
-    kern<<<grid, kWarps * 32, smem, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+    kern<<<grid, W * 32, smem, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
     return cudaGetLastError();
+}
+
+static int g_fp_warps = 0;  // warps per CTA of the SIMD-FastPFOR decoder (0 = default)
+
+void set_fastpfor_warps(int w) { g_fp_warps = (w == 4 || w == 8) ? w : 0; }
+
+template <int DELTA>
+static cudaError_t launch_fp_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
+                               WsHeader* h, cudaStream_t s) {
+    const int w = g_fp_warps ? g_fp_warps : 8;
+    if (w == 4) return launch_fp<DELTA, 4>(in, in_bytes, out, n, index, h, s);
+    return launch_fp<DELTA, 8>(in, in_bytes, out, n, index, h, s);
 }
 
 cudaError_t launch_fastpfor_decode(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                    const uint64_t* index, WsHeader* h, cudaStream_t s) {
-    if (delta == ICX_DELTA_1) return launch_fp<ICX_DELTA_1>(in, in_bytes, out, n, index, h, s);
-    if (delta == ICX_DELTA_4) return launch_fp<ICX_DELTA_4>(in, in_bytes, out, n, index, h, s);
-    return launch_fp<ICX_DELTA_NONE>(in, in_bytes, out, n, index, h, s);
+    if (delta == ICX_DELTA_1) return launch_fp_w<ICX_DELTA_1>(in, in_bytes, out, n, index, h, s);
+    if (delta == ICX_DELTA_4) return launch_fp_w<ICX_DELTA_4>(in, in_bytes, out, n, index, h, s);
+    return launch_fp_w<ICX_DELTA_NONE>(in, in_bytes, out, n, index, h, s);
 }
 
 }  // namespace icx

@@ -11,6 +11,8 @@ namespace icx {
 constexpr uint32_t kBlocksPerPage = 512;
 constexpr uint32_t kUnitsPerPage = kBlocksPerPage / 16;
 constexpr int kUnitMax = 16 * 16 * 32;  // packed bytes of 16 blocks at width 32
+constexpr int kExScratch = 16 * 128;    // owner block of each exception of a unit (bytes)
+constexpr int kExScratchBytes = kExScratch + 32;  // then 16 x uint16 exceptions-before-block
 constexpr int kFBuf = kUnitMax + 128;
 
 __device__ __forceinline__ uint32_t ld32(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
@@ -403,7 +405,7 @@ __device__ __forceinline__ void parse_small_page(SmallPageSmem& S, const uint8_t
 // j of block k is element cursor + j of exception array d = maxbits - b of
 // the page (at pbase + pg[d - 1], vertical layout: chunk e/128, lane e%4,
 // field (e%128)/4), its position the j-th byte after pos_off.  The patch rows
-// reuse `buf` once unpacked; blk_of is a 2048-byte scratch.
+// reuse `buf` once unpacked; blk_of is a kExScratchBytes scratch.
 __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__ in, uint64_t pbase,
                                                      const uint32_t* __restrict__ pg, const BlockMeta* m,
                                                      uint32_t K, uint8_t* buf, uint8_t* blk_of, uint4 (&v)[16],
@@ -428,11 +430,13 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
     if (C) {
         // patch: high << b of every exception of the unit (Sec. 5)
         __syncwarp();
-        uint32_t pre[16];
+        // pre[k]: the unit's exceptions before block k (kept in the scratch
+        // after blk_of, so the gathers below hold no table in registers)
+        uint16_t* pre = reinterpret_cast<uint16_t*>(blk_of + kExScratch);
         uint32_t run = 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            pre[k] = run;
+            if (lane == 0) pre[k] = (uint16_t)run;
             const uint32_t c = (uint32_t)k < K ? m[k].c : 0u;
             for (uint32_t j = lane; j < c; j += 32) blk_of[run + j] = (uint8_t)k;
             if (c) reinterpret_cast<uint4*>(buf + 512 * k)[lane] = make_uint4(0, 0, 0, 0);
@@ -451,11 +455,7 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
                 if (q < C) {
                     const uint32_t k = blk_of[q];
                     const BlockMeta mk = m[k];
-                    uint32_t pk = 0;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if ((uint32_t)j == k) pk = pre[j];
-                    const uint32_t jj = q - pk;
+                    const uint32_t jj = q - pre[k];
                     const uint32_t d = mk.d, e = mk.cursor + jj;
                     const uint8_t* arr = in + pbase + pg[d - 1] + 16 * (size_t)d * (e >> 7);
                     const uint32_t ii = e & 127, bit = (ii >> 2) * d;

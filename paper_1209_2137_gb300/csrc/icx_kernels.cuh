@@ -26,5 +26,6 @@ cudaError_t launch_fastpfor_encode(int delta, const uint32_t* x, size_t n, uint8
 size_t fastpfor_encode_workspace_bytes(size_t n);
 void set_bp128_warps(int w);
 void set_bp128_prefetch(int on);
+void set_fastpfor_warps(int w);
 
 }  // namespace icx
