@@ -267,10 +267,15 @@ __device__ __forceinline__ void lookback_publish(WsHeader* h, uint32_t epoch, ui
                    ((unsigned long long)tag << 32) | comp(agg, lane));
 }
 
+// Predecessors read per look-back round: 32 x this.  Measured on the 2^26
+// sorted workloads, one row (32 predecessors) beats 2 and 4: the window's
+// loads and registers cost more than the extra rounds they save.
+constexpr int kLookbackRows = 1;
+
 // Resolves the exclusive prefix of `tile` (whose aggregate `agg` is already
 // published) from its predecessors' states and, if `publish`, publishes its
 // inclusive prefix.  Whole warp.
-template <int NL, int R = 4>
+template <int NL, int R = kLookbackRows>
 __device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg, bool publish = true) {
     static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
@@ -352,7 +357,7 @@ __device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, ui
 
 // Decoupled look-back of one tile: publish its aggregate, resolve its
 // exclusive prefix, publish its inclusive prefix.  Whole warp.
-template <int NL, int R = 4>
+template <int NL, int R = kLookbackRows>
 __device__ __forceinline__ uint4 lookback(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg) {
     lookback_publish<NL>(h, epoch, tile, agg);
     return lookback_resolve<NL, R>(h, epoch, tile, agg);
