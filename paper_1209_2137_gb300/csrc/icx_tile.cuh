@@ -27,6 +27,8 @@ struct TileShared {
 // of block k in v[k]); `residue` means the values arrive in W32 residue
 // ownership and are moved to row ownership here.  Returns the unit aggregate
 // (stride 1: .x; stride 4: one per residue).
+constexpr int kScanGroup = 8;  // blocks whose stride-1 scans are interleaved (8 or 16 measure the same)
+
 template <int DELTA>
 __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, bool residue, int lane) {
     // The 16 blocks' scans are independent except for the carry between
@@ -74,30 +76,36 @@ __device__ __forceinline__ uint4 unit_local_scan(uint4 (&v)[16], uint32_t K, boo
         for (int k = 0; k < 16; ++k) v[k] = residue_to_row(v[k], lane);
     }
     if (DELTA == ICX_DELTA_1) {
-        uint32_t incl[16], tot[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            v[k].y += v[k].x;
-            v[k].z += v[k].y;
-            v[k].w += v[k].z;
-            incl[k] = v[k].w;
-        }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t y = __shfl_up_sync(FULL, incl[k], off);
-                if (lane >= off) incl[k] += y;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) tot[k] = __shfl_sync(FULL, incl[k], 31);
+        // two groups of 8 blocks, each with its 8 scans interleaved step by
+        // step: enough independent shuffles in flight, half the temporaries
         uint32_t carry = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const uint32_t add = carry + incl[k] - v[k].w;
-            v[k] = make_uint4(v[k].x + add, v[k].y + add, v[k].z + add, v[k].w + add);
-            carry += tot[k];
+        for (int g = 0; g < 16; g += kScanGroup) {
+            uint32_t incl[kScanGroup];
+#pragma unroll
+            for (int i = 0; i < kScanGroup; ++i) {
+                uint4& x = v[g + i];
+                x.y += x.x;
+                x.z += x.y;
+                x.w += x.z;
+                incl[i] = x.w;
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int i = 0; i < kScanGroup; ++i) {
+                    const uint32_t y = __shfl_up_sync(FULL, incl[i], off);
+                    if (lane >= off) incl[i] += y;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kScanGroup; ++i) {
+                const uint32_t tot = __shfl_sync(FULL, incl[i], 31);
+                uint4& x = v[g + i];
+                const uint32_t add = carry + incl[i] - x.w;
+                x = make_uint4(x.x + add, x.y + add, x.z + add, x.w + add);
+                carry += tot;
+            }
         }
         agg.x = carry;
     } else if (DELTA == ICX_DELTA_4) {
