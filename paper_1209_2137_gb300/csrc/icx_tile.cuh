@@ -173,9 +173,10 @@ __device__ __forceinline__ uint4 tile_agg_scan(const TileShared& S, uint4& mine,
 // Stride-4 scan of a whole unit in row ownership through an 8 KB shared
 // scratch (the warp's staging buffer, free after unpacking): the 16 x 32 x 4
 // values are written in position order, each lane then owns two columns
-// (block k = lane/2, residues 2*(lane&1) and +1) and scans them down the 32
-// rows serially, one shuffle scan over the blocks adds the column carries,
-// and the values are read back in row ownership.  Word (k, t, c) lives at
+// (block k = lane/2, residues 2*(lane&1) and +1): one pass down the 32 rows
+// sums them, one shuffle scan over the blocks gives the column carries, a
+// second pass writes the running sums back in place, and the values are read
+// back in row ownership.  Word (k, t, c) lives at
 // 128k + 4(t ^ (k & 7)) + c, which keeps both the 128-bit row accesses and
 // the 64-bit column accesses free of bank conflicts.  Returns the unit's
 // four residue aggregates.
@@ -186,15 +187,13 @@ __device__ __forceinline__ uint4 unit_scan_d4_smem(uint4 (&v)[16], uint32_t* scr
     __syncwarp();
     const int k = lane >> 1, c0 = 2 * (lane & 1);
     uint32_t* col = scratch + 128 * k + c0;
-    uint32_t x[32], y[32];
+    // pass 1: the two column totals
     uint32_t sx = 0, sy = 0;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
         const uint2 e = *reinterpret_cast<const uint2*>(col + 4 * (t ^ (k & 7)));
         sx += e.x;
         sy += e.y;
-        x[t] = sx;
-        y[t] = sy;
     }
     // carries of the earlier blocks: exclusive scan over k (lanes of one parity)
     uint32_t ix = sx, iy = sy;
@@ -206,10 +205,16 @@ __device__ __forceinline__ uint4 unit_scan_d4_smem(uint4 (&v)[16], uint32_t* scr
             iy += b;
         }
     }
-    const uint32_t ex = ix - sx, ey = iy - sy;
+    // pass 2: running sums written back in place (no register copy of the columns)
+    uint32_t rx = ix - sx, ry = iy - sy;
 #pragma unroll
-    for (int t = 0; t < 32; ++t)
-        *reinterpret_cast<uint2*>(col + 4 * (t ^ (k & 7))) = make_uint2(x[t] + ex, y[t] + ey);
+    for (int t = 0; t < 32; ++t) {
+        uint2* p = reinterpret_cast<uint2*>(col + 4 * (t ^ (k & 7)));
+        const uint2 e = *p;
+        rx += e.x;
+        ry += e.y;
+        *p = make_uint2(rx, ry);
+    }
     __syncwarp();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk)
