@@ -636,8 +636,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64)",
-        "config": {"workload": "long sorted uint32 arrays (sample), 12 decodes per step",
-                   "parallelism": "single CPU thread"},
+        "config": {"workload": workload_label(arrays, [{"label": c[3]} for c in COMBOS for _ in arrays]),
+                   "parallelism": "single CPU thread", "sample_per_step": sample},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
