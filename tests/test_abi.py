@@ -87,3 +87,13 @@ def test_plan_create_rejects_bad_lists(lib):
     with pytest.raises(icx.IcxError) as e:
         icx.Plan([empty], {"warps_per_cta": 6, "order": 0, "l2_prefetch": 0})
     assert e.value.code == icx.EINVAL
+
+
+def test_tuning_keys(lib):
+    # host-side settings: known keys accepted, unknown refused
+    import paper_1209_2137_gb300 as icx
+    for key, value in [("bp128.warps_per_cta", 0), ("bp128.l2_prefetch", 1), ("fastpfor.warps_per_cta", 0)]:
+        icx.set_tuning(key, value)
+    with pytest.raises(icx.IcxError) as e:
+        icx.set_tuning("no.such.key", 1)
+    assert e.value.code == icx.EINVAL

@@ -1,0 +1,61 @@
+"""GPU parity of every launch variant the tuning keys select: the same
+streams decode bit for bit to the oracle's decode with SIMD-BP128 / W32 at 4,
+8 and 16 warps per CTA, with and without the L2 prefetch ahead, and with
+SIMD-FastPFOR at 4 and 8 warps per CTA."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1209_2137_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1209_2137_gb300 as icx  # noqa: E402
+
+N = 3 * 65536 + 2048 * 7 + 77  # several tiles of every width, a partial metablock and a tail
+
+
+@pytest.fixture(scope="module")
+def streams():
+    x = W.uniform_sorted(N, 27, 91)
+    out = []
+    for codec, delta, fmt in [("bp128", 1, 0), ("bp128", 4, 0), ("bp128", 1, 1), ("bp128", 4, 1), ("fastpfor", 1, 0),
+                              ("fastpfor", 4, 0)]:
+        enc = oracle.encode(codec, x, delta, fmt)
+        out.append((codec, delta, fmt, enc, oracle.index(codec, enc, N, fmt), oracle.decode(codec, enc, N, delta, fmt)))
+    return out
+
+
+def decode(codec, delta, fmt, enc, idx):
+    d = torch.from_numpy(enc).cuda()
+    ix = torch.from_numpy(idx.view(np.int64)).cuda()
+    ws = icx.Workspace(N)
+    if codec == "bp128":
+        y = icx.bp128_decode(d, N, delta, fmt, ix.view(torch.uint64), workspace=ws)
+    else:
+        y = icx.fastpfor_decode(d, N, delta, ix.view(torch.uint64), workspace=ws)
+    assert ws.status() == icx.OK
+    return y.cpu().numpy().view(np.uint32)
+
+
+def test_every_launch_variant_matches_oracle(streams):
+    try:
+        for warps in (4, 8, 16):
+            for l2 in (0, 1):
+                icx.set_tuning("bp128.warps_per_cta", warps)
+                icx.set_tuning("bp128.l2_prefetch", l2)
+                for codec, delta, fmt, enc, idx, want in streams:
+                    if codec == "bp128":
+                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (warps, l2, delta, fmt)
+        for warps in (4, 8):
+            icx.set_tuning("fastpfor.warps_per_cta", warps)
+            for codec, delta, fmt, enc, idx, want in streams:
+                if codec == "fastpfor":
+                    assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (warps, delta)
+    finally:
+        icx.set_tuning("bp128.warps_per_cta", 0)
+        icx.set_tuning("bp128.l2_prefetch", 1)
+        icx.set_tuning("fastpfor.warps_per_cta", 0)
