@@ -43,7 +43,10 @@ COMBOS = [
     ("fastpfor", 1, 0, "SIMD-FastPFOR"),
     ("fastpfor", 4, 0, "SIMD-FastPFOR*"),
 ]
-KERNEL_NAMES = {"bp128": "bp128_decode_kernel", "fastpfor": "fastpfor_decode_kernel"}
+def kernel_name(codec: str, delta: int) -> str:
+    if codec == "bp128":
+        return "bp128_decode_kernel"
+    return "fastpfor_decode_pipe_kernel" if delta == 4 else "fastpfor_decode_kernel"
 
 
 def log(*a):
@@ -309,7 +312,7 @@ def run_gpu(args, world, rank, local):
     traffic = recorded_traffic(f"{ds['array']}:{ds['label']}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"{KERNEL_NAMES[ds['codec']]} ({ds['label']}, {ds['array']})",
+                "kernel": f"{kernel_name(ds['codec'], ds['delta'])} ({ds['label']}, {ds['array']})",
                 "alg_bytes_per_launch": ds["alg_bytes"], "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"}
     headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
 

@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         load_context();
         tile = next;
     }
-    if (broken) mbar_wait(bar, phase);
+    if (broken) mbar_wait(bar, phase ^ 1);  // the parity of the wait that timed out
     finish_launch(h, epoch);
 }
 

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         tile = next;
     }
     // a copy that never landed must not outlive the CTA's shared memory
-    if (broken) mbar_wait(bar, phase);
+    if (broken) mbar_wait(bar, phase ^ 1);  // the parity of the wait that timed out
     finish_launch(h, epoch);
 }
 
