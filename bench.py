@@ -309,7 +309,8 @@ def run_gpu(args, world, rank, local):
     ds = streams[dom]
     dom_ms = float(np.mean(per[:, dom]))
     achieved = ds["alg_bytes"] / (dom_ms / 1e3) / 1e9
-    traffic = recorded_traffic(f"{ds['array']}:{ds['label']}")
+    # recorded at the default sizes only
+    traffic = None if args.n else recorded_traffic(f"{ds['array']}:{ds['label']}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"{kernel_name(ds['codec'], ds['delta'])} ({ds['label']}, {ds['array']})",
