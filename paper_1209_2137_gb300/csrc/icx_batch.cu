@@ -75,7 +75,7 @@ static_assert(sizeof(BatchShared) + 8 * kMaxWarps <= kBatchHdr, "batch header");
 // ---------------------------------------------------------------- kernels
 
 // Pages of more than kSmallK blocks: one CTA each (items: list, page).
-__global__ void __launch_bounds__(kMetaThreads)
+__global__ void __launch_bounds__(kMetaThreads, 7)
     batch_meta_kernel(const ListDev* __restrict__ lists, const uint2* __restrict__ pages,
                       BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
                       ulonglong2* __restrict__ ranges, WsHeader* h) {
@@ -473,6 +473,10 @@ static cudaError_t batch_occupancy(int W, int* blocks, int* sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    // the page parse wants 7 CTAs of 30 KB per SM
+    e = cudaFuncSetAttribute(batch_meta_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     if (W == 4) {
         e = cudaFuncSetAttribute(batch_decode_kernel<4, false, CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
@@ -1269,7 +1273,9 @@ icx_status icx_server_create(const icx_list_desc* pool, size_t nlists, size_t bu
             return fail(ICX_ECUDA);
     }
     const int smem = kBatchHdr + sv->W * kWarpBytes;
-    cudaError_t e;
+    cudaError_t e = cudaFuncSetAttribute(batch_meta_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return fail(ICX_ECUDA);
     if (sv->W == 4) {
         e = cudaFuncSetAttribute(batch_decode_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)

@@ -73,7 +73,7 @@ __global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_
 
 // ------------------------------------------------------------ page parse
 
-__global__ void __launch_bounds__(kMetaThreads)
+__global__ void __launch_bounds__(kMetaThreads, 7)
     fastpfor_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n, const uint64_t* __restrict__ index,
                          BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
                          WsHeader* h) {
@@ -390,6 +390,10 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
     static int sms = 0;
     if (blocks_per_sm < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        // the page parse wants 7 CTAs of 30 KB per SM
+        e = cudaFuncSetAttribute(fastpfor_meta_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);

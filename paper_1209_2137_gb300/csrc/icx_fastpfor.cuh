@@ -37,15 +37,16 @@ constexpr uint32_t kMetaSpan = kMetaWin + 1024;  // bytes held per window
 constexpr uint32_t kRecMax = 132;  // longest record the chain follows (c > 128 is corrupt anyway)
 constexpr uint32_t kGroups = kBlocksPerPage / 8;
 
+// 30 KB, so that 7 CTAs fit an SM and a 2^26-integer stream's 1,024 pages
+// are parsed at once on 152 SMs.
 struct MetaSmem {
     uint32_t bytes[kMetaSpan / 4 + 4];  // window of the byte array (zero past its end)
-    uint32_t j1[kMetaSpan / 4];         // record length at each position, one byte each
     uint16_t ja[kMetaSpan];             // J2, then J8
     uint16_t jb[kMetaSpan];             // J4
     uint32_t grp[kGroups];              // start of records 8g .. 8g+7
     uint32_t start[kBlocksPerPage];     // record starts
     uint32_t bmc[kBlocksPerPage];       // b | maxbits << 8 | c << 16
-    uint32_t poff[kBlocksPerPage];      // page-relative offset of the packed low bits
+    uint2 urng[kUnitsPerPage];          // per unit: packed offset of its first block, end of its last
     uint32_t wcnt[kMetaThreads / 32][32];  // per warp, exceptions per width
     uint32_t wpk[kMetaThreads / 32];       // per warp, sum of b
     uint32_t ctl[4];                       // window start, next group, chain state
@@ -53,6 +54,12 @@ struct MetaSmem {
 
 __device__ __forceinline__ uint32_t rec_len(uint32_t b, uint32_t mb, uint32_t c) {
     return mb > b ? 3u + min(c, 129u) : 2u;
+}
+
+// Length of the record that would start at byte i of the staged window.
+__device__ __forceinline__ uint32_t rec_len_at(const uint32_t* bytes, uint32_t i) {
+    const uint32_t x = __funnelshift_r(bytes[i >> 2], bytes[(i >> 2) + 1], 8 * (i & 3));
+    return rec_len(x & 0xFF, (x >> 8) & 0xFF, (x >> 16) & 0xFF);
 }
 
 // Whole warp: the exception arrays after a page's byte array.  Their offsets
@@ -124,7 +131,6 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
                                            ulonglong2* __restrict__ rng = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint8_t* sb = reinterpret_cast<const uint8_t*>(S.bytes);
-    const uint8_t* s1 = reinterpret_cast<const uint8_t*>(S.j1);
     const uint32_t G = (K + 7) / 8;
 
     bool bad = !(base <= end && end <= in_bytes && (base & 15) == 0 && end - base >= 16);
@@ -157,25 +163,15 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         g0 = S.ctl[1];
         if (g0 >= G || S.ctl[3]) break;
         const uint32_t Lw = L - ws;  // > 0: the chain only continues at starts < L
-        const uint32_t lim8 = min(kMetaWin, Lw), lim4 = lim8 + 4 * kRecMax, lim2 = lim4 + 2 * kRecMax,
-                       lim1 = lim2 + kRecMax;
+        const uint32_t lim8 = min(kMetaWin, Lw), lim4 = lim8 + 4 * kRecMax, lim2 = lim4 + 2 * kRecMax;
         const uint32_t nw = ws < Lpad ? min(kMetaSpan / 4, (Lpad - ws) / 4) : 0u;
         for (uint32_t i = tid; i < kMetaSpan / 4 + 4; i += kMetaThreads) S.bytes[i] = i < nw ? __ldg(arr + ws / 4 + i) : 0u;
         __syncthreads();
-        for (uint32_t w = tid; w < (lim1 + 3) / 4; w += kMetaThreads) {
-            const uint32_t lo = S.bytes[w], hi = S.bytes[w + 1];
-            uint32_t packed = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t x = __funnelshift_r(lo, hi, 8 * j);
-                packed |= rec_len(x & 0xFF, (x >> 8) & 0xFF, (x >> 16) & 0xFF) << (8 * j);
-            }
-            S.j1[w] = packed;
-        }
-        __syncthreads();
+        // J2 straight from the bytes (i + a + 3 <= lim2 + kRecMax + 2 stays
+        // inside the window's words)
         for (uint32_t i = tid; i < lim2; i += kMetaThreads) {
-            const uint32_t a = s1[i];
-            S.ja[i] = (uint16_t)(a + s1[i + a]);
+            const uint32_t a = rec_len_at(S.bytes, i);
+            S.ja[i] = (uint16_t)(a + rec_len_at(S.bytes, i + a));
         }
         __syncthreads();
         for (uint32_t i = tid; i < lim4; i += kMetaThreads) {
@@ -212,9 +208,10 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
             uint32_t q = S.grp[g] - ws;
             const uint32_t k1 = min(K, 8 * g + 8);
             for (uint32_t k = 8 * g; k < k1; ++k) {
+                const uint32_t b = sb[q], mb = sb[q + 1], c = sb[q + 2];
                 S.start[k] = ws + q;
-                S.bmc[k] = sb[q] | (uint32_t)sb[q + 1] << 8 | (uint32_t)sb[q + 2] << 16;
-                q += s1[q];
+                S.bmc[k] = b | mb << 8 | c << 16;
+                q += rec_len(b, mb, c);
             }
         }
         __syncthreads();
@@ -280,7 +277,8 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
                 m.c = (uint8_t)c_[i];
                 m.flags = 0;
                 pm[k] = m;
-                S.poff[k] = m.packed_off;
+                if (k % 16 == 0) S.urng[k / 16].x = m.packed_off;
+                if (k % 16 == 15 || k == K - 1) S.urng[k / 16].y = m.packed_off + 16 * b_[i];
             }
         }
     }
@@ -292,9 +290,8 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
     if ((uint32_t)tid < nunits) {
         uint2 x = make_uint2(0, ~0u);
         if (!bad) {
-            const uint32_t k0 = 16 * tid, k1 = min(K, k0 + 16) - 1;
-            const uint32_t first = S.poff[k0];
-            x = make_uint2(first, S.poff[k1] + 16 * (S.bmc[k1] & 0xFF) - first);
+            const uint2 r = S.urng[tid];
+            x = make_uint2(r.x, r.y - r.x);
             um[tid] = x;
         }
         if (rng) rng[tid] = make_ulonglong2(bad ? 0ull : reinterpret_cast<uint64_t>(page + x.x), x.y);
