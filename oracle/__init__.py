@@ -72,6 +72,7 @@ def _load():
             lib.orc_fastpfor_encode.argtypes, lib.orc_fastpfor_encode.restype = [u32p, sz, i, u8p], sz
             lib.orc_fastpfor_decode.argtypes, lib.orc_fastpfor_decode.restype = [u8p, sz, sz, i, u32p], i
             lib.orc_fastpfor_index.argtypes, lib.orc_fastpfor_index.restype = [u8p, sz, sz, u64p], i
+            lib.orc_member_bits.argtypes, lib.orc_member_bits.restype = [u32p, sz, u32p, sz, u32p, u64p], None
             _lib = lib
     return _lib
 
@@ -251,3 +252,16 @@ def index(codec: str, data, n: int, layout: int = PAPER) -> np.ndarray:
     if codec == "fastpfor":
         return fastpfor_index(data, n)
     raise ValueError(codec)
+
+
+# -- Sec. 7: decoding fused into a consumer (sorted-list membership) ---------
+
+def member_bits(a, b):
+    """Membership of the sorted query list b in the sorted list a, by merging
+    the two: returns (bits, count), bit j of the uint32 words `bits` (bit j%32
+    of word j//32) set iff b[j] occurs in a; count = number of set bits."""
+    va, vb = _u32(a), _u32(b)
+    bits = np.zeros(max(1, (vb.size + 31) // 32), dtype=np.uint32)
+    cnt = np.zeros(1, dtype=np.uint64)
+    _load().orc_member_bits(_ptr(va), va.size, _ptr(vb), vb.size, _ptr(bits), _ptr(cnt))
+    return bits[: (vb.size + 31) // 32].copy(), int(cnt[0])

@@ -541,3 +541,20 @@ int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta,
     free(d);
     return rc;
 }
+
+/* ---------------------------------------------------------------- Sec. 7 */
+
+void orc_member_bits(const uint32_t *a, size_t na, const uint32_t *b, size_t nb, uint32_t *bits,
+                     uint64_t *count) {
+    size_t i = 0;
+    uint64_t c = 0;
+    for (size_t w = 0; w < (nb + 31) / 32; ++w) bits[w] = 0;
+    for (size_t j = 0; j < nb; ++j) {
+        while (i < na && a[i] < b[j]) ++i; /* a[i] is the first element >= b[j] */
+        if (i < na && a[i] == b[j]) {
+            bits[j / 32] |= 1u << (j % 32);
+            ++c;
+        }
+    }
+    *count = c;
+}

@@ -85,6 +85,15 @@ int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta,
 size_t orc_fastpfor_index_len(size_t n);
 int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
 
+/* Sec. 7 (decoding fused into its consumer; intersections of sorted
+ * arrays): membership of the sorted query list b[0..nb) in the sorted list
+ * a[0..na), by the textbook merge of two sorted arrays.  Bit j of
+ * bits[0..ceil(nb/32)) (bit j%32 of word j/32) is set iff b[j] equals some
+ * a[i]; bits past nb stay 0; *count = the number of set bits.  Both lists
+ * must be non-decreasing. */
+void orc_member_bits(const uint32_t *a, size_t na, const uint32_t *b, size_t nb, uint32_t *bits,
+                     uint64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

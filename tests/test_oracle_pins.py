@@ -426,3 +426,58 @@ def test_fastpfor_padding_overhead_range():
         unpadded += sum(d * c for d, (c, _) in pg["arrays"].items())
     overhead = (8 * enc.size - unpadded) / x.size
     assert 0.0 <= overhead < 1.0
+
+
+# -- Sec. 7: sorted-list membership (the consumer fused with decoding) -------
+
+def _member_brute(a, b):
+    s = set(int(v) for v in a)
+    flags = [int(v) in s for v in b]
+    bits = np.zeros(max(1, (len(b) + 31) // 32), dtype=np.uint32)
+    for j, f in enumerate(flags):
+        if f:
+            bits[j // 32] |= np.uint32(1 << (j % 32))
+    return bits[: (len(b) + 31) // 32], sum(flags)
+
+
+def test_member_bits_brute_force_with_duplicates():
+    # tiny sorted lists with repeated values on both sides, values drawn from
+    # a small range so that hits, misses and runs all occur
+    rng = np.random.default_rng(5)
+    for t in range(300):
+        na, nb = int(rng.integers(0, 40)), int(rng.integers(0, 70))
+        hi = int(rng.integers(1, 60))
+        a = np.sort(rng.integers(0, hi, na)).astype(np.uint32)
+        b = np.sort(rng.integers(0, hi + 5, nb)).astype(np.uint32)
+        bits, cnt = oracle.member_bits(a, b)
+        want_bits, want_cnt = _member_brute(a, b)
+        assert cnt == want_cnt, t
+        assert np.array_equal(bits, want_bits), t
+
+
+def test_member_bits_special_cases():
+    a = np.arange(0, 1000, 3, dtype=np.uint32)
+    bits, cnt = oracle.member_bits(a, np.zeros(0, np.uint32))
+    assert bits.size == 0 and cnt == 0
+    b = np.arange(0, 100, dtype=np.uint32)
+    bits, cnt = oracle.member_bits(np.zeros(0, np.uint32), b)
+    assert cnt == 0 and not bits.any()
+    bits, cnt = oracle.member_bits(a, a)  # b a subset of a: every bit set
+    assert cnt == a.size and int(sum(bin(int(w)).count("1") for w in bits)) == a.size
+    bits, cnt = oracle.member_bits(a, a + 1)  # disjoint
+    assert cnt == 0 and not bits.any()
+    # bits past nb stay zero; the extremes of the value range
+    b = np.array([0, 5, 0xFFFFFFFE, 0xFFFFFFFF], dtype=np.uint32)
+    bits, cnt = oracle.member_bits(np.array([0, 0xFFFFFFFF], np.uint32), b)
+    assert cnt == 2 and bits.tolist() == [0b1001]
+
+
+def test_member_bits_matches_isin():
+    # a special case that reduces to a library routine: numpy's isin
+    x = W.uniform_sorted(200000, 24, 33)
+    rng = np.random.default_rng(9)
+    b = np.sort(np.concatenate([rng.choice(x, 5000), rng.integers(0, 1 << 24, 5000).astype(np.uint32)]))
+    bits, cnt = oracle.member_bits(x, b)
+    flags = np.isin(b, x)
+    got = np.unpackbits(bits.view(np.uint8), bitorder="little")[: b.size].astype(bool)
+    assert np.array_equal(got, flags) and cnt == int(flags.sum())
