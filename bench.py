@@ -319,6 +319,7 @@ def run_gpu(args, world, rank, local):
 
     e2e = run_e2e(args, streams, out, ws, dev, world)
     exceptions = None if args.skip_exceptions else run_exceptions(args, out, ws, flush_l2, world)
+    intersect = None if args.skip_intersect else run_intersect(args, streams, arrays, out, ws, flush_l2, world)
     batched = serving = None
     if not args.skip_batch:
         del out
@@ -343,6 +344,7 @@ def run_gpu(args, world, rank, local):
         "headline_kernel": kern[headline],
         "e2e": e2e,
         "exceptions": exceptions,
+        "intersect": intersect,
         "batched": batched,
         "serving": serving,
         "gpu_launches": launches_per_step * K,
@@ -449,6 +451,80 @@ def run_exceptions(args, out, ws, flush_l2, world):
                       "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
     res["note"] = "the GPU encoders write the oracle's bytes (tests), so bits_per_int is the oracle's"
     log(f"[bench] exception-heavy: SIMD-FastPFOR {res['SIMD-FastPFOR']}, SIMD-BP128 {res['SIMD-BP128']}")
+    return res
+
+
+# ------------------------------------------------- decode into a consumer --
+
+def run_intersect(args, streams, arrays, out, ws, flush_l2, world):
+    """Decoding fused into a consumer (Sec. 7): membership of a sorted query
+    list of ~2^22 integers (half drawn from the list) in the 2^26-integer
+    uniform list, from its SIMD-BP128* and SIMD-BP128 streams.  Fused: one
+    bp128_intersect call (the decoded integers are never written); unfused:
+    bp128_decode into HBM, then sorted_intersect over the decoded list."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+    from paper_1209_2137_gb300 import workloads as W
+
+    x = arrays.get("uniform")
+    if x is None:
+        return None
+    q = W.query_list(x, 1 << 22, 29, W.SEED_BASE + 6)
+    pos = np.minimum(np.searchsorted(x, q), x.size - 1)
+    hits = int(np.count_nonzero(x[pos] == q))
+    b = torch.from_numpy(q).to(out.device)
+    bits = torch.empty((q.size + 31) // 32, dtype=torch.uint32, device=out.device)
+    bits2 = torch.empty_like(bits)
+    cnt = torch.empty(1, dtype=torch.uint64, device=out.device)
+    cnt2 = torch.empty_like(cnt)
+    o = out[: x.size]
+    peak, _ = peaks()
+    res = {"workload": f"sorted query list of {q.size} distinct integers (half drawn from the list, half uniform "
+                       f"in [0, 2^29)) against the uniform list of {x.size}", "n": int(x.size), "nb": int(q.size),
+           "hits": hits, "streams": []}
+    steps = max(3, min(args.steps, 50))
+    for st in streams:
+        if st["array"] != "uniform" or st["codec"] != "bp128" or st["fmt"] != icx.FMT_PAPER:
+            continue
+        e = st["enc"]
+
+        def fused():
+            icx.bp128_intersect(e.data, e.n, b, e.delta, e.fmt, index=e.index, bits=bits, count=cnt, workspace=ws)
+
+        def unfused():
+            icx.bp128_decode(e.data, e.n, e.delta, e.fmt, index=e.index, out=o, workspace=ws)
+            icx.sorted_intersect(o, b, bits=bits2, count=cnt2)
+
+        fused()
+        unfused()
+        ws.raise_status("intersect")
+        c1, c2 = int(cnt.cpu().view(torch.int64)[0]), int(cnt2.cpu().view(torch.int64)[0])
+        if c1 != hits or c2 != hits or not torch.equal(bits, bits2):
+            raise SystemExit(f"intersect {st['label']}: verification failed ({c1}, {c2}, want {hits})")
+        times = {}
+        for name, fn in (("fused", fused), ("unfused", unfused)):
+            for _ in range(args.warmup):
+                flush_l2()
+                fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, z in ev:
+                flush_l2()
+                a.record()
+                fn()
+                z.record()
+            torch.cuda.synchronize()
+            times[name] = max_over_ranks(float(np.mean([a.elapsed_time(z) for a, z in ev])), world)
+        ws.raise_status("intersect")
+        stream_b = e.nbytes + 8 * e.index.numel()
+        alg = stream_b + 4 * q.size + 4 * bits.numel()  # stream + query list + bitmap
+        res["streams"].append({
+            "codec": st["label"], "fused_ms": round(times["fused"], 4), "unfused_ms": round(times["unfused"], 4),
+            "speedup": round(times["unfused"] / times["fused"], 3),
+            "fused_gints_s": round(x.size / (times["fused"] / 1e3) / 1e9, 1),
+            "fused_achieved_gbs": round(alg / (times["fused"] / 1e3) / 1e9, 1),
+            "fused_frac": round(alg / (times["fused"] / 1e3) / 1e9 / peak, 4)})
+    log(f"[bench] intersect: {res['streams']}")
     return res
 
 
@@ -663,6 +739,7 @@ def main():
     ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
     ap.add_argument("--fastpfor-warps", type=int, default=0, help="warps per CTA of the SIMD-FastPFOR decoder")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
+    ap.add_argument("--skip-intersect", action="store_true", help="skip the decode-into-intersection leg")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
     ap.add_argument("--batch-lists", type=int, default=65536)
     ap.add_argument("--batch-total", type=int, default=1 << 28)

@@ -146,6 +146,34 @@ icx_status fastpfor_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out
 icx_status delta_decode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_delta delta,
                         void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
 
+/* ---------------------------------------------- decode into a consumer -- */
+
+/* Membership of a sorted query list in a compressed sorted list, with the
+ * decode fused into the consumer (Sec. 7: an integrated decode, and
+ * intersections of sorted arrays as the query that consumes the integers).
+ * Let a[0..n) be the integers the SIMD-BP128 / W32 stream d_in decodes to
+ * (arguments d_in .. d_index, d_workspace as for bp128_decode).  Bit j of
+ * d_bits (bit j%32 of word j/32; ceil(nb/32) words) is set iff d_b[j] equals
+ * some a[i], every other bit is cleared, and *d_count (device) receives the
+ * number of set bits: the set bits select the intersection of a and b from
+ * d_b in order.  The decoded integers are written nowhere.
+ * Both a and d_b[0..nb) must be non-decreasing (sorted lists; duplicates are
+ * allowed); otherwise the bits are unspecified, but every access stays
+ * inside the given buffers.  d_b and d_bits need 4-byte, d_count 8-byte,
+ * d_in, d_index and the workspace 16-byte alignment.  Data errors of the
+ * stream go to the workspace status word as for bp128_decode.  n == 0 or
+ * nb == 0 clear the outputs and launch nothing else. */
+icx_status bp128_intersect(const uint8_t *d_in, size_t in_bytes, size_t n, icx_delta delta,
+                           icx_layout fmt, const uint64_t *d_index, const uint32_t *d_b, size_t nb,
+                           uint32_t *d_bits, uint64_t *d_count, void *d_workspace,
+                           size_t workspace_bytes, icx_stream_t stream);
+
+/* The same consumer on a list that is already decoded: d_a[0..n)
+ * (non-decreasing, 16-byte aligned) in place of the stream.  The unfused
+ * path is bp128_decode followed by this call. */
+icx_status sorted_intersect(const uint32_t *d_a, size_t n, const uint32_t *d_b, size_t nb,
+                            uint32_t *d_bits, uint64_t *d_count, icx_stream_t stream);
+
 /* Allocation-free variant of bp128_decode for callers that cannot allocate
  * device memory -- code that must not call cudaMalloc (an allocation-free
  * runtime, a host application that owns every device allocation, a plugin

@@ -66,6 +66,8 @@ def lib():
                 "fastpfor_index": ([vp, sz, sz, vp, vp, sz, vp], i),
                 "bp128_decode": ([vp, sz, vp, sz, i, i, vp, vp, sz, vp], i),
                 "fastpfor_decode": ([vp, sz, vp, sz, i, vp, vp, sz, vp], i),
+                "bp128_intersect": ([vp, sz, sz, i, i, vp, vp, sz, vp, vp, vp, sz, vp], i),
+                "sorted_intersect": ([vp, sz, vp, sz, vp, vp, vp], i),
                 "delta_decode": ([vp, vp, sz, i, vp, sz, vp], i),
                 "delta_encode": ([vp, vp, sz, i, vp], i),
                 "bp128_encode": ([vp, sz, i, i, vp, sz, vp, vp, vp, sz, vp], i),
@@ -92,7 +94,8 @@ def lib():
 
 EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_bytes", "icx_fastpfor_max_bytes",
             "icx_workspace_bytes", "icx_encode_workspace_bytes", "icx_workspace_init", "icx_status_read",
-            "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "delta_decode", "delta_encode",
+            "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "bp128_intersect",
+            "sorted_intersect", "delta_decode", "delta_encode",
             "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning", "icx_plan_create",
             "icx_plan_error_list", "icx_plan_launch", "icx_plan_launch_per_list", "icx_plan_status", "icx_plan_tuning",
             "icx_plan_destroy", "icx_server_create", "icx_server_run", "icx_server_destroy")
@@ -241,6 +244,44 @@ def fastpfor_decode(data, n: int, delta: int = DELTA_1, index=None, out=None, wo
     _check(lib().fastpfor_decode(_ptr(data), nbytes, _ptr(out), n, delta, _ptr(index), ws.ptr(), ws.bytes,
                                  _stream(stream)), "fastpfor_decode")
     return out
+
+
+def _member_out(b, bits, count):
+    import torch
+    _dev(b, torch.uint32, "b")
+    if bits is None:
+        bits = torch.empty((b.numel() + 31) // 32, dtype=torch.uint32, device=b.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.uint64, device=b.device)
+    _dev(bits, torch.uint32, "bits")
+    _dev(count, torch.uint64, "count")
+    return bits, count
+
+
+def bp128_intersect(data, n: int, b, delta: int = DELTA_1, fmt: int = FMT_PAPER, index=None, bits=None,
+                    count=None, workspace=None, stream=None, in_bytes=None):
+    """Membership of the sorted query list b in the sorted list the stream
+    decodes to, decoded and consumed in one pass (Sec. 7).  Returns (bits,
+    count): bit j of the uint32 words `bits` set iff b[j] is in the list;
+    count (a one-element uint64 tensor on the device) the number of set bits."""
+    import torch
+    _dev(data, torch.uint8, "data")
+    bits, count = _member_out(b, bits, count)
+    ws = _ws(workspace, n, stream)
+    nbytes = data.numel() if in_bytes is None else in_bytes
+    _check(lib().bp128_intersect(_ptr(data), nbytes, n, delta, fmt, _ptr(index), _ptr(b), b.numel(), _ptr(bits),
+                                 _ptr(count), ws.ptr(), ws.bytes, _stream(stream)), "bp128_intersect")
+    return bits, count
+
+
+def sorted_intersect(a, b, bits=None, count=None, stream=None):
+    """The same consumer over the decoded sorted list a (the unfused path)."""
+    import torch
+    _dev(a, torch.uint32, "a")
+    bits, count = _member_out(b, bits, count)
+    _check(lib().sorted_intersect(_ptr(a), a.numel(), _ptr(b), b.numel(), _ptr(bits), _ptr(count),
+                                  _stream(stream)), "sorted_intersect")
+    return bits, count
 
 
 def delta_decode(d, delta: int = DELTA_1, out=None, workspace=None, stream=None):

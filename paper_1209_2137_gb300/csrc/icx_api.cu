@@ -101,6 +101,50 @@ icx_status bp128_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, s
     return from_cuda(icx::launch_bp128_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s));
 }
 
+// Clears the bitmap and the count of a membership call.
+static icx_status member_clear(uint32_t* d_bits, size_t nb, uint64_t* d_count, cudaStream_t s) {
+    if (nb && cudaMemsetAsync(d_bits, 0, 4 * ((nb + 31) / 32), s) != cudaSuccess) return ICX_ECUDA;
+    return from_cuda(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
+}
+
+static bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+icx_status bp128_intersect(const uint8_t* d_in, size_t in_bytes, size_t n, icx_delta delta, icx_layout fmt,
+                           const uint64_t* d_index, const uint32_t* d_b, size_t nb, uint32_t* d_bits,
+                           uint64_t* d_count, void* d_ws, size_t ws_bytes, icx_stream_t stream) {
+    if (!valid_delta(delta) || !valid_fmt(fmt) || n > kMaxN || nb > kMaxN || !d_count) return ICX_EINVAL;
+    if (nb && (!d_b || !d_bits)) return ICX_EINVAL;
+    if (!aligned(d_count, 8) || (nb && (!aligned(d_b, 4) || !aligned(d_bits, 4)))) return ICX_EALIGN;
+    if (n && (!d_in || !d_ws)) return ICX_EINVAL;
+    if (n && (!aligned16(d_in) || !aligned16(d_ws) || (d_index && !aligned16(d_index)))) return ICX_EALIGN;
+    if (n && ws_bytes < icx_workspace_bytes(n)) return ICX_ENOSPC;
+    cudaStream_t s = (cudaStream_t)stream;
+    const icx_status cl = member_clear(d_bits, nb, d_count, s);
+    if (cl != ICX_OK || n == 0 || nb == 0) return cl;
+    WsHeader* h = static_cast<WsHeader*>(d_ws);
+    if (!d_index) {
+        if (metablocks(n) > 1) return ICX_EINVAL;
+        const icx_status st = from_cuda(icx::launch_bp128_index(d_in, in_bytes, n, fmt, h->mini_index, h, s));
+        if (st != ICX_OK) return st;
+        d_index = h->mini_index;
+    }
+    return from_cuda(icx::launch_bp128_member(delta, fmt, d_in, in_bytes, n, d_index, d_b, nb, d_bits,
+                                              reinterpret_cast<unsigned long long*>(d_count), h, s));
+}
+
+icx_status sorted_intersect(const uint32_t* d_a, size_t n, const uint32_t* d_b, size_t nb, uint32_t* d_bits,
+                            uint64_t* d_count, icx_stream_t stream) {
+    if (n > kMaxN || nb > kMaxN || !d_count || (n && !d_a)) return ICX_EINVAL;
+    if (nb && (!d_b || !d_bits)) return ICX_EINVAL;
+    if (!aligned(d_count, 8) || (nb && (!aligned(d_b, 4) || !aligned(d_bits, 4))) || (n && !aligned16(d_a)))
+        return ICX_EALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    const icx_status cl = member_clear(d_bits, nb, d_count, s);
+    if (cl != ICX_OK || n == 0 || nb == 0) return cl;
+    return from_cuda(
+        icx::launch_sorted_member(d_a, n, d_b, nb, d_bits, reinterpret_cast<unsigned long long*>(d_count), s));
+}
+
 icx_status delta_decode(const uint32_t* d_in, uint32_t* d_out, size_t n, icx_delta delta, void* d_ws,
                         size_t ws_bytes, icx_stream_t stream) {
     if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;

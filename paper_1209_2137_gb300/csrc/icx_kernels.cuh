@@ -22,6 +22,11 @@ cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, 
 cudaError_t launch_fastpfor_encode(int delta, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
                                    uint64_t* index, uint64_t* out_bytes, void* ws, size_t ws_bytes,
                                    cudaStream_t s);
+cudaError_t launch_bp128_member(int delta, int fmt, const uint8_t* in, size_t in_bytes, size_t n,
+                                const uint64_t* index, const uint32_t* b, size_t nb, uint32_t* bits,
+                                unsigned long long* count, WsHeader* h, cudaStream_t s);
+cudaError_t launch_sorted_member(const uint32_t* a, size_t n, const uint32_t* b, size_t nb, uint32_t* bits,
+                                 unsigned long long* count, cudaStream_t s);
 
 size_t fastpfor_encode_workspace_bytes(size_t n);
 void set_bp128_warps(int w);

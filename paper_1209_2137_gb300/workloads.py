@@ -182,3 +182,25 @@ def posting_lists(nlists: int = 65536, total: int = 1 << 28, lo: int = 128, hi: 
         R = min(n << int(beta[i]), 1 << 32)
         values[offsets[i]:offsets[i + 1]] = distinct_sorted(n, R, seed * 1000003 + i)
     return L, offsets, values, bp
+
+
+def query_list(x: np.ndarray, nq: int, range_bits: int, seed: int, hit_frac: float = 0.5,
+               distinct: bool = True) -> np.ndarray:
+    """A sorted query list for intersecting with the sorted list x: about
+    hit_frac * nq elements of x (positions drawn uniformly, with
+    replacement) and the rest uniform in [0, 2^range_bits); sorted, and
+    deduplicated if `distinct` (a posting list), else with its repeats."""
+    nh = int(round(nq * hit_frac)) if x.size else 0
+    z = splitmix64(seed, 0, nq)
+    pos = (z[:nh] % np.uint64(max(1, x.size))).astype(np.int64)
+    rest = _top_bits(z[nh:], range_bits).astype(np.uint32)
+    q = np.concatenate([x[pos].astype(np.uint32), rest])
+    return _sorted_distinct(q) if distinct else np.sort(q)
+
+
+def workload_intersect(seed: int = SEED_BASE + 6):
+    """The intersection workload: the 2^26-integer uniform list (values in
+    [0, 2^29)) and a sorted distinct query list of about 2^22 integers, half
+    of them drawn from the list (Sec. 7: lists of very different lengths)."""
+    x = workload_uniform_long()
+    return x, query_list(x, 1 << 22, 29, seed)
