@@ -73,6 +73,10 @@ def _load():
             lib.orc_fastpfor_decode.argtypes, lib.orc_fastpfor_decode.restype = [u8p, sz, sz, i, u32p], i
             lib.orc_fastpfor_index.argtypes, lib.orc_fastpfor_index.restype = [u8p, sz, sz, u64p], i
             lib.orc_member_bits.argtypes, lib.orc_member_bits.restype = [u32p, sz, u32p, sz, u32p, u64p], None
+            lib.orc_bp32_max_bytes.argtypes, lib.orc_bp32_max_bytes.restype = [sz], sz
+            lib.orc_bp32_encode.argtypes, lib.orc_bp32_encode.restype = [u32p, sz, i, u8p], sz
+            lib.orc_bp32_decode.argtypes, lib.orc_bp32_decode.restype = [u8p, sz, sz, i, u32p], i
+            lib.orc_bp32_index.argtypes, lib.orc_bp32_index.restype = [u8p, sz, sz, u64p], i
             _lib = lib
     return _lib
 
@@ -180,6 +184,35 @@ def bp128_index(data, n: int, layout: int = PAPER) -> np.ndarray:
     return out
 
 
+# -- Sec. 6.2: BP32 ----------------------------------------------------------
+
+def bp32_encode(x, delta: int) -> np.ndarray:
+    v = _u32(x)
+    lib = _load()
+    out = np.zeros(lib.orc_bp32_max_bytes(v.size), dtype=np.uint8)
+    n = lib.orc_bp32_encode(_ptr(v), v.size, delta, _ptr(out))
+    return out[:n].copy()
+
+
+def bp32_decode(data, n: int, delta: int) -> np.ndarray:
+    d = _u8(data)
+    out = np.zeros(n, dtype=np.uint32)
+    rc = _load().orc_bp32_decode(_ptr(d), d.size, n, delta, _ptr(out))
+    if rc != 0:
+        raise CorruptStream(f"bp32 stream corrupt (rc={rc})")
+    return out
+
+
+def bp32_index(data, n: int) -> np.ndarray:
+    d = _u8(data)
+    lib = _load()
+    out = np.zeros(lib.orc_bp128_index_len(n), dtype=np.uint64)
+    rc = lib.orc_bp32_index(_ptr(d), d.size, n, _ptr(out))
+    if rc != 0:
+        raise CorruptStream(f"bp32 stream corrupt (rc={rc})")
+    return out
+
+
 # -- Sec. 5: (SIMD-)FastPFOR -------------------------------------------------
 
 def fastpfor_choose(values):
@@ -230,9 +263,12 @@ def fastpfor_index(data, n: int) -> np.ndarray:
     return out
 
 
+BP32 = 2  # layout value of the BP32 format in the SIMD-BP128 calls
+
+
 def encode(codec: str, x, delta: int, layout: int = PAPER) -> np.ndarray:
     if codec == "bp128":
-        return bp128_encode(x, delta, layout)
+        return bp32_encode(x, delta) if layout == BP32 else bp128_encode(x, delta, layout)
     if codec == "fastpfor":
         return fastpfor_encode(x, delta)
     raise ValueError(codec)
@@ -240,7 +276,7 @@ def encode(codec: str, x, delta: int, layout: int = PAPER) -> np.ndarray:
 
 def decode(codec: str, data, n: int, delta: int, layout: int = PAPER) -> np.ndarray:
     if codec == "bp128":
-        return bp128_decode(data, n, delta, layout)
+        return bp32_decode(data, n, delta) if layout == BP32 else bp128_decode(data, n, delta, layout)
     if codec == "fastpfor":
         return fastpfor_decode(data, n, delta)
     raise ValueError(codec)
@@ -248,7 +284,7 @@ def decode(codec: str, data, n: int, delta: int, layout: int = PAPER) -> np.ndar
 
 def index(codec: str, data, n: int, layout: int = PAPER) -> np.ndarray:
     if codec == "bp128":
-        return bp128_index(data, n, layout)
+        return bp32_index(data, n) if layout == BP32 else bp128_index(data, n, layout)
     if codec == "fastpfor":
         return fastpfor_index(data, n)
     raise ValueError(codec)

@@ -542,6 +542,81 @@ int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta,
     return rc;
 }
 
+/* ------------------------------------------------------- Sec. 6.2: BP32 */
+
+size_t orc_bp32_max_bytes(size_t n) { return (n / 128) * (4 + 4 * 4 * 32) + 5 * (n % 128) + 16; }
+
+size_t orc_bp32_encode(const uint32_t *x, size_t n, int delta, uint8_t *out) {
+    uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    orc_delta_encode(x, n, delta, d);
+    size_t meta = n / 128, pos = 0;
+    for (size_t m = 0; m < meta; ++m) {
+        uint8_t *desc = out + pos;
+        int b[4];
+        for (int j = 0; j < 4; ++j) {
+            b[j] = block_width(d + 128 * m + 32 * j, 32);
+            desc[j] = (uint8_t)b[j]; /* byte j of the little-endian descriptor word */
+        }
+        pos += 4;
+        for (int j = 0; j < 4; ++j) {
+            orc_pack(d + 128 * m + 32 * j, 32, 1, b[j], out + pos);
+            pos += 4 * (size_t)b[j];
+        }
+    }
+    pos += orc_vbyte_encode(d + 128 * meta, n - 128 * meta, out + pos);
+    free(d);
+    return pos;
+}
+
+/* Size of the BP32 metablock at `pos`, or 0 if it is corrupt or truncated. */
+static size_t bp32_meta_size(const uint8_t *in, size_t in_bytes, size_t pos) {
+    if (pos + 4 > in_bytes) return 0;
+    size_t size = 4;
+    for (int j = 0; j < 4; ++j) {
+        if (in[pos + j] > 32) return 0;
+        size += 4 * (size_t)in[pos + j];
+    }
+    return pos + size <= in_bytes ? size : 0;
+}
+
+int orc_bp32_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index) {
+    size_t meta = n / 128, pos = 0;
+    for (size_t m = 0; m < meta; ++m) {
+        size_t size = bp32_meta_size(in, in_bytes, pos);
+        if (size == 0) return ORC_ECORRUPT;
+        if (m % 16 == 0) index[m / 16] = pos;
+        pos += size;
+    }
+    index[(meta + 15) / 16] = pos;
+    return ORC_OK;
+}
+
+int orc_bp32_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x) {
+    uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    size_t meta = n / 128, pos = 0;
+    int rc = ORC_OK;
+    for (size_t m = 0; m < meta; ++m) {
+        size_t size = bp32_meta_size(in, in_bytes, pos);
+        if (size == 0) {
+            rc = ORC_ECORRUPT;
+            break;
+        }
+        size_t off = pos + 4;
+        for (int j = 0; j < 4; ++j) {
+            orc_unpack(in + off, 32, 1, in[pos + j], d + 128 * m + 32 * j);
+            off += 4 * (size_t)in[pos + j];
+        }
+        pos += size;
+    }
+    if (rc == ORC_OK) {
+        size_t used = orc_vbyte_decode(in + pos, in_bytes - pos, n - 128 * meta, d + 128 * meta);
+        if (used == (size_t)-1) rc = ORC_ECORRUPT;
+    }
+    if (rc == ORC_OK) orc_delta_decode(d, n, delta, x);
+    free(d);
+    return rc;
+}
+
 /* ---------------------------------------------------------------- Sec. 7 */
 
 void orc_member_bits(const uint32_t *a, size_t na, const uint32_t *b, size_t nb, uint32_t *bits,

@@ -85,6 +85,18 @@ int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta,
 size_t orc_fastpfor_index_len(size_t n);
 int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
 
+/* Sec. 6.2, BP32 (the paper's scalar binary packing; R20): n/128 metablocks
+ * of 128 integers, each a 32-bit little-endian descriptor (byte j = width
+ * b_j of block j, j = 0..3) followed by blocks 0..3 of 32 integers, block j
+ * packed LSB-first into b_j 32-bit words (one lane, orc_pack with lanes = 1);
+ * then the n % 128 remaining integers in Variable Byte (R1).  The index has
+ * an entry every 16 metablocks (2,048 integers) and one for the tail:
+ * orc_bp128_index_len(n) entries. */
+size_t orc_bp32_max_bytes(size_t n);
+size_t orc_bp32_encode(const uint32_t *x, size_t n, int delta, uint8_t *out);
+int orc_bp32_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x);
+int orc_bp32_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
+
 /* Sec. 7 (decoding fused into its consumer; intersections of sorted
  * arrays): membership of the sorted query list b[0..nb) in the sorted list
  * a[0..na), by the textbook merge of two sorted arrays.  Bit j of

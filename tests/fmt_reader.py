@@ -76,3 +76,23 @@ def fastpfor_walk(buf, n):
                           bitset=bitset, arrays=arrays, size=end - base))
         pos = end
     return pages, pos
+
+
+def bp32_read(buf, n):
+    """BP32 (Sec. 6.2): per 128-integer metablock a little-endian descriptor
+    word (byte j = width of 32-integer block j) and four blocks of b_j words,
+    integer i of a block at bits [i*b, (i+1)*b) of the block's words taken as
+    one little-endian bit string.  Returns (metablocks as (offset, widths),
+    the n//128*128 coded deltas, tail offset), read with Python integers."""
+    buf = bytes(memoryview(buf))
+    metas, deltas, pos = [], [], 0
+    for _ in range(n // 128):
+        widths = list(buf[pos:pos + 4])
+        metas.append((pos, widths))
+        off = pos + 4
+        for b in widths:
+            bits = int.from_bytes(buf[off:off + 4 * b], "little")
+            deltas.extend((bits >> (i * b)) & ((1 << b) - 1) for i in range(32))
+            off += 4 * b
+        pos = off
+    return metas, deltas, pos

@@ -481,3 +481,62 @@ def test_member_bits_matches_isin():
     flags = np.isin(b, x)
     got = np.unpackbits(bits.view(np.uint8), bitorder="little")[: b.size].astype(bool)
     assert np.array_equal(got, flags) and cnt == int(flags.sum())
+
+
+# -- Sec. 6.2: BP32 (scalar binary packing, NEXT-3) --------------------------
+
+def _vbyte_len(v):
+    return max(1, (int(v).bit_length() + 6) // 7)
+
+
+def test_bp32_bytes_read_back_independently():
+    # the bytes, read with Python integers from the format definition, give
+    # the deltas whose closed-form prefix sums are the input; every width
+    # byte is the largest bit length of its 32 deltas; sizes are closed form
+    for n in [0, 1, 127, 128, 129, 255, 256, 2047, 2048, 2049, 4096 + 77, 16 * 128 * 3 + 5]:
+        x = W.uniform_sorted(n, 26, 400 + n % 97) if n else np.zeros(0, np.uint32)
+        for delta in (0, 1, 4):
+            enc = oracle.bp32_encode(x, delta)
+            metas, deltas, tail = F.bp32_read(enc, n)
+            s = delta if delta else 1
+            xi = [int(v) for v in x]
+            want = [xi[i] - (xi[i - s] if (delta and i >= s) else 0) for i in range(n)]
+            want = [w % (1 << 32) for w in want]
+            assert deltas == want[: 128 * (n // 128)], (n, delta)
+            for m, (off, widths) in enumerate(metas):
+                for j, b in enumerate(widths):
+                    blk = want[128 * m + 32 * j: 128 * m + 32 * j + 32]
+                    assert b == max(v.bit_length() for v in blk), (n, delta, m, j)
+            size = sum(4 + 4 * sum(w) for _, w in metas) + sum(_vbyte_len(v) for v in want[128 * (n // 128):])
+            assert enc.size == size == tail + sum(_vbyte_len(v) for v in want[128 * (n // 128):])
+            assert np.array_equal(oracle.bp32_decode(enc, n, delta), x)
+            idx = oracle.bp32_index(enc, n)
+            assert list(idx[:-1]) == [metas[16 * u][0] for u in range((n // 128 + 15) // 16)]
+            assert int(idx[-1]) == tail
+
+
+def test_bp32_every_width_single_bit_fields():
+    # brute force: each width 0..32, a single set bit in each of the 32
+    # positions of block 2 of a metablock
+    for b in range(33):
+        for i in range(32):
+            d = np.zeros(128, np.uint32)
+            if b:
+                d[64 + i] = np.uint32(1 << (b - 1))
+            enc = oracle.bp32_encode(d, 0)
+            assert list(enc[:4]) == [0, 0, b, 0]
+            assert np.array_equal(oracle.bp32_decode(enc, 128, 0), d)
+            if b:
+                bitpos = 8 * (4 + 0) + i * b + (b - 1)  # block 2 starts right after the descriptor
+                assert (int.from_bytes(enc.tobytes(), "little") >> bitpos) & 1 == 1
+
+
+def test_bp32_corrupt_rejected():
+    x = W.uniform_sorted(1000, 20, 6)
+    enc = oracle.bp32_encode(x, 1)
+    bad = enc.copy()
+    bad[0] = 33
+    with pytest.raises(oracle.CorruptStream):
+        oracle.bp32_decode(bad, x.size, 1)
+    with pytest.raises(oracle.CorruptStream):
+        oracle.bp32_decode(enc[:100], x.size, 1)
