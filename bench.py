@@ -320,6 +320,7 @@ def run_gpu(args, world, rank, local):
     e2e = run_e2e(args, streams, out, ws, dev, world)
     exceptions = None if args.skip_exceptions else run_exceptions(args, out, ws, flush_l2, world)
     intersect = None if args.skip_intersect else run_intersect(args, streams, arrays, out, ws, flush_l2, world)
+    bp32 = None if args.skip_bp32 else run_bp32(args, arrays, out, ws, flush_l2, world)
     batched = serving = None
     if not args.skip_batch:
         del out
@@ -345,6 +346,7 @@ def run_gpu(args, world, rank, local):
         "e2e": e2e,
         "exceptions": exceptions,
         "intersect": intersect,
+        "bp32": bp32,
         "batched": batched,
         "serving": serving,
         "gpu_launches": launches_per_step * K,
@@ -451,6 +453,51 @@ def run_exceptions(args, out, ws, flush_l2, world):
                       "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
     res["note"] = "the GPU encoders write the oracle's bytes (tests), so bits_per_int is the oracle's"
     log(f"[bench] exception-heavy: SIMD-FastPFOR {res['SIMD-FastPFOR']}, SIMD-BP128 {res['SIMD-BP128']}")
+    return res
+
+
+# ------------------------------------------------------------------ BP32 --
+
+def run_bp32(args, arrays, out, ws, flush_l2, world):
+    """BP32 (Sec. 6.2: scalar binary packing of 32-integer blocks, 4 per
+    128-integer metablock) on the long sorted arrays, stride 1 (the paper's
+    differential coding for it) and stride 4."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+
+    peak, _ = peaks()
+    res = {"workload": "the long sorted arrays of the main step, BP32 streams encoded on the GPU", "streams": []}
+    steps = max(3, min(args.steps, 50))
+    for name, x in arrays.items():
+        xt = torch.from_numpy(x).to(out.device)
+        o = out[: x.size]
+        for delta, label in ((icx.DELTA_1, "BP32"), (icx.DELTA_4, "BP32*")):
+            e = icx.bp128_encode(xt, delta, icx.FMT_BP32)
+            icx.decode(e, out=o, workspace=ws)
+            ws.raise_status("BP32 decode")
+            if not torch.equal(o, xt):
+                raise SystemExit(f"{label} {name}: verification failed")
+            for _ in range(args.warmup):
+                flush_l2()
+                icx.decode(e, out=o, workspace=ws)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, z in ev:
+                flush_l2()
+                a.record()
+                icx.decode(e, out=o, workspace=ws)
+                z.record()
+            torch.cuda.synchronize()
+            ms = max_over_ranks(float(np.mean([a.elapsed_time(z) for a, z in ev])), world)
+            alg = e.nbytes + 8 * e.index.numel() + 4 * x.size
+            res["streams"].append({"array": name, "codec": label, "n": int(x.size),
+                                   "bits_per_int": round(8.0 * e.nbytes / x.size, 3), "ms": round(ms, 4),
+                                   "gints_s": round(x.size / (ms / 1e3) / 1e9, 1),
+                                   "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1),
+                                   "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)})
+            del e
+        del xt
+    log(f"[bench] BP32: {res['streams']}")
     return res
 
 
@@ -740,6 +787,7 @@ def main():
     ap.add_argument("--fastpfor-warps", type=int, default=0, help="warps per CTA of the SIMD-FastPFOR decoder")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
     ap.add_argument("--skip-intersect", action="store_true", help="skip the decode-into-intersection leg")
+    ap.add_argument("--skip-bp32", action="store_true", help="skip the BP32 decodes")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
     ap.add_argument("--batch-lists", type=int, default=65536)
     ap.add_argument("--batch-total", type=int, default=1 << 28)

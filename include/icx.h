@@ -78,7 +78,15 @@ typedef enum {
 } icx_status;
 
 typedef enum { ICX_DELTA_NONE = 0, ICX_DELTA_1 = 1, ICX_DELTA_4 = 4 } icx_delta;
-typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1 } icx_layout;
+/* Stream layouts of the SIMD-BP128 calls: the paper's SIMD-BP128 (4-lane
+ * vertical blocks of 128 integers, 16 per metablock, Sec. 4 and 6.2), the
+ * W32 variant (32 lanes interleaved word by word, not in the paper), and the
+ * paper's scalar BP32 (Sec. 6.2): metablocks of 128 integers, each a 32-bit
+ * little-endian descriptor (byte j = width of 32-integer block j) and four
+ * blocks of 32 integers packed LSB-first in b_j words; the n % 128 last
+ * integers in Variable Byte.  A BP32 index entry marks every 16th metablock
+ * (2,048 integers), so the index lengths agree. */
+typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1, ICX_FMT_BP32 = 2 } icx_layout;
 
 /* ------------------------------------------------------------- sizes ---- */
 
@@ -159,7 +167,8 @@ icx_status delta_decode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_del
  * d_b in order.  The decoded integers are written nowhere.
  * Both a and d_b[0..nb) must be non-decreasing (sorted lists; duplicates are
  * allowed); otherwise the bits are unspecified, but every access stays
- * inside the given buffers.  d_b and d_bits need 4-byte, d_count 8-byte,
+ * inside the given buffers.  fmt is ICX_FMT_PAPER or ICX_FMT_W32 (BP32:
+ * ICX_EINVAL).  d_b and d_bits need 4-byte, d_count 8-byte,
  * d_in, d_index and the workspace 16-byte alignment.  Data errors of the
  * stream go to the workspace status word as for bp128_decode.  n == 0 or
  * nb == 0 clear the outputs and launch nothing else. */
@@ -259,7 +268,8 @@ typedef enum { ICX_CODEC_BP128 = 0, ICX_CODEC_FASTPFOR = 1 } icx_codec;
  * output); d_index: its metablock / page index as built by bp128_index,
  * fastpfor_index or the encoders; it may be NULL where the single-array call
  * allows it (at most one metablock / page).  delta: icx_delta; fmt:
- * icx_layout (SIMD-BP128 only, else ignored).  The caller owns all buffers
+ * icx_layout (SIMD-BP128 only: ICX_FMT_PAPER or ICX_FMT_W32, else
+ * ICX_EINVAL; ignored for SIMD-FastPFOR).  The caller owns all buffers
  * and keeps them alive and unmodified while the plan is in use. */
 typedef struct {
     const uint8_t *d_in;

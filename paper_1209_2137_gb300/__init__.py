@@ -24,7 +24,7 @@ OK, EINVAL, EALIGN, ECORRUPT, ENOSPC, ECUDA, ETIMEOUT = range(7)
 STATUS_NAMES = {0: "ICX_OK", 1: "ICX_EINVAL", 2: "ICX_EALIGN", 3: "ICX_ECORRUPT", 4: "ICX_ENOSPC",
                 5: "ICX_ECUDA", 6: "ICX_ETIMEOUT"}
 DELTA_NONE, DELTA_1, DELTA_4 = 0, 1, 4
-FMT_PAPER, FMT_W32 = 0, 1
+FMT_PAPER, FMT_W32, FMT_BP32 = 0, 1, 2
 CODEC_BP128, CODEC_FASTPFOR = 0, 1
 
 _lock = threading.Lock()

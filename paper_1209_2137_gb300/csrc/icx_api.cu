@@ -14,7 +14,7 @@ constexpr size_t kMaxN = (size_t)1 << 34;  // bound that keeps every size in ran
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool valid_delta(int d) { return d == ICX_DELTA_NONE || d == ICX_DELTA_1 || d == ICX_DELTA_4; }
-bool valid_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_W32; }
+bool valid_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_W32 || f == ICX_FMT_BP32; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 icx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ICX_OK : ICX_ECUDA; }
@@ -22,10 +22,11 @@ icx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ICX_OK : ICX_ECU
 size_t metablocks(size_t n) { return (n / 128 + 15) / 16; }
 size_t pages(size_t n) { return (n / 128 + 511) / 512; }
 
-// encode workspace: header, then widths (1 byte per block), then sizes
-// (4 bytes per metablock or page, plus one).
+// encode workspace: header, then widths (1 byte per 128-integer block; BP32:
+// one 4-width descriptor word per 128 integers), then sizes (4 bytes per
+// metablock or page, plus one).
 size_t enc_widths_off() { return icx::kWsHeaderBytes; }
-size_t enc_sizes_off(size_t n) { return enc_widths_off() + round_up(n / 128 + 1, 256); }
+size_t enc_sizes_off(size_t n) { return enc_widths_off() + round_up(4 * (n / 128 + 1), 256); }
 
 }  // namespace
 
@@ -36,7 +37,7 @@ size_t icx_fastpfor_index_len(size_t n) { return pages(n) + 1; }
 
 size_t icx_bp128_max_bytes(size_t n, icx_layout fmt) {
     const size_t M = metablocks(n), nb = n / 128;
-    const size_t body = fmt == ICX_FMT_W32 ? M * (16 + 128 * 64) : M * 16 + nb * 512;
+    const size_t body = fmt == ICX_FMT_W32 ? M * (16 + 128 * 64) : fmt == ICX_FMT_BP32 ? nb * 516 : M * 16 + nb * 512;
     return body + (n % 128) * 5 + 16;
 }
 
@@ -112,7 +113,8 @@ static bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
 icx_status bp128_intersect(const uint8_t* d_in, size_t in_bytes, size_t n, icx_delta delta, icx_layout fmt,
                            const uint64_t* d_index, const uint32_t* d_b, size_t nb, uint32_t* d_bits,
                            uint64_t* d_count, void* d_ws, size_t ws_bytes, icx_stream_t stream) {
-    if (!valid_delta(delta) || !valid_fmt(fmt) || n > kMaxN || nb > kMaxN || !d_count) return ICX_EINVAL;
+    if (!valid_delta(delta) || !valid_fmt(fmt) || fmt == ICX_FMT_BP32 || n > kMaxN || nb > kMaxN || !d_count)
+        return ICX_EINVAL;
     if (nb && (!d_b || !d_bits)) return ICX_EINVAL;
     if (!aligned(d_count, 8) || (nb && (!aligned(d_b, 4) || !aligned(d_bits, 4)))) return ICX_EALIGN;
     if (n && (!d_in || !d_ws)) return ICX_EINVAL;

@@ -48,11 +48,41 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     if (threadIdx.x == 0) S.nx[0] = atomicAdd(&h->tile_counter, 1u);
     __syncthreads();
     uint32_t phase = 0, it = 0;
+    uint32_t shift = 0;   // BP32: the unit's offset inside its 16-byte aligned copy
     bool broken = false;  // a copy of this warp never landed: decode nothing more
     // starts the bulk copy of metablock uu; returns its size, ~0u for an
     // invalid index entry, 0 if there is nothing to copy
     auto issue = [&](uint32_t uu) -> uint32_t {
         uint32_t size = 0;
+        if (FMT == ICX_FMT_BP32) {
+            // BP32 units are 4-byte aligned: the 16-byte aligned interior
+            // [off & ~15, end & ~15) by bulk copy (possibly empty: the barrier
+            // is then armed with no bytes), the last end % 16 bytes by plain
+            // loads; nothing past `end` is read
+            uint64_t off = 0, end = 0;
+            if (uu < M && !broken && lane == 0) {
+                off = index[uu];
+                end = index[uu + 1];
+                const bool ok = off <= end && end <= in_bytes && end - off >= 4 &&
+                                end - (off & ~15ull) <= (uint64_t)(kBp32UnitMax + 15) && ((off | end) & 3) == 0;
+                size = ok ? (uint32_t)(end - off) : ~0u;
+                if (ok) {
+                    const uint64_t a0 = off & ~15ull, a1 = end & ~15ull;
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, a1 > a0 ? (uint32_t)(a1 - a0) : 0u);
+                    if (a1 > a0) bulk_load(buf, in + a0, (uint32_t)(a1 - a0), bar);
+                }
+            }
+            size = __shfl_sync(FULL, size, 0);
+            off = __shfl_sync(FULL, off, 0);
+            end = __shfl_sync(FULL, end, 0);
+            if (size != 0 && size != ~0u) {
+                const uint64_t a0 = off & ~15ull, a1 = end & ~15ull;
+                if ((uint64_t)lane < end - a1) buf[a1 - a0 + lane] = __ldg(in + a1 + lane);
+                shift = (uint32_t)(off - a0);
+            }
+            return size;
+        }
         if (uu < M && !broken && lane == 0) {
             const uint64_t off = index[uu], end = index[uu + 1];
             const bool ok = off <= end && end <= in_bytes && end - off >= 16 && end - off <= kMetaMax &&
@@ -101,7 +131,11 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
                 ((pf_off | pf_end) & 15) == 0)
                 prefetch_l2(in + pf_off, (uint32_t)(pf_end - pf_off));
             if (ok) {
-                ok = bp128_unpack_unit<FMT>(buf, size, K, v, h, lane);
+                __syncwarp();  // BP32: the plainly loaded last bytes
+                if (FMT == ICX_FMT_BP32)
+                    ok = bp32_unpack_unit(buf + shift, size, K, v, h, lane);
+                else
+                    ok = bp128_unpack_unit<FMT>(buf, size, K, v, h, lane);
                 residue = ok && FMT == ICX_FMT_W32;
             }
             __syncwarp();
@@ -124,7 +158,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
                 lookback_publish<NL>(h, epoch, tile, shfl4(incl, W - 1));
             }
         }
-        if (DELTA == ICX_DELTA_4 && FMT == ICX_FMT_PAPER)
+        if (DELTA == ICX_DELTA_4 && FMT != ICX_FMT_W32)  // row ownership
             unit_scan_d4_smem(v, reinterpret_cast<uint32_t*>(buf), lane);
         else
             unit_local_scan<DELTA>(v, K, residue, lane);
@@ -164,6 +198,23 @@ __global__ void bp128_index_kernel(const uint8_t* __restrict__ in, size_t in_byt
         index[m] = pos;
         if (bad) continue;
         const size_t K = min((size_t)16, nb - 16 * m);
+        if (fmt == ICX_FMT_BP32) {  // K metablocks of 128 integers, each 4 + 4 * (sum of 4 widths) bytes
+            for (size_t k = 0; k < K && !bad; ++k) {
+                if (pos + 4 > in_bytes) {
+                    bad = true;
+                    break;
+                }
+                size_t size = 4;
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t b = in[pos + j];
+                    if (b > 32) bad = true;
+                    size += 4 * (size_t)b;
+                }
+                if (pos + size > in_bytes) bad = true;
+                pos += size;
+            }
+            continue;
+        }
         if (pos + 16 > in_bytes) {
             bad = true;
             continue;
@@ -185,9 +236,6 @@ __global__ void bp128_index_kernel(const uint8_t* __restrict__ in, size_t in_byt
 
 // ------------------------------------------------------ standalone delta
 
-// Tile = 8 warps x 2048 integers; lanes load row-owned uint4s (coalesced),
-// scan, look back, store.  In place is safe: every element is read and
-// written by the same lane.
 // CTA tiles of kWarps x 2048 integers: coalesced 128-bit loads in row
 // ownership, local scan, one look-back per tile, stores.  In place is safe:
 // every element is read and written by the same lane.
@@ -250,15 +298,6 @@ static cudaError_t launch_bp128(const uint8_t* in, size_t in_bytes, uint32_t* ou
     return cudaGetLastError();
 }
 
-
-
-
-
-
-
-
-  // warps per CTA of the SIMD-BP128 decoder (0 = per-stride default)
-
 void set_bp128_warps(int w) { g_bp128_warps = (w == 4 || w == 8 || w == 16) ? w : 0; }
 
 
@@ -267,11 +306,9 @@ void set_bp128_prefetch(int on) { g_bp128_l2_ahead = on != 0; }
 template <int DELTA, int FMT>
 static cudaError_t launch_bp128_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                   const uint64_t* index, WsHeader* h, cudaStream_t s) {
-    // measured on the 2^26 sorted workload: 4 warps per CTA suit the stride-4
-    // scan (more CTAs per SM), 8 the others
     // measured on the 2^26 sorted workloads: 4 warps per CTA for the paper
-    // layout, 8 for W32
-    const int w = g_bp128_warps ? g_bp128_warps : (FMT == ICX_FMT_PAPER ? 4 : 8);
+    // layout (and BP32, also row ownership), 8 for W32
+    const int w = g_bp128_warps ? g_bp128_warps : (FMT == ICX_FMT_W32 ? 8 : 4);
     if (w == 4) return launch_bp128<DELTA, FMT, 4>(in, in_bytes, out, n, index, h, s);
     if (w == 16) return launch_bp128<DELTA, FMT, 16>(in, in_bytes, out, n, index, h, s);
     return launch_bp128<DELTA, FMT, 8>(in, in_bytes, out, n, index, h, s);
@@ -287,6 +324,9 @@ cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_W32)
     ICX_CASE(ICX_DELTA_1, ICX_FMT_W32)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_W32)
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_BP32)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_BP32)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_BP32)
 #undef ICX_CASE
     return cudaErrorInvalidValue;
 }

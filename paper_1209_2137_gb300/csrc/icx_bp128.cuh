@@ -10,6 +10,8 @@ namespace icx {
 
 constexpr int kMetaMax = 16 + 16 * 16 * 32;  // 8208: every width 32
 constexpr int kBuf = kMetaMax + 128;         // slack for reading one row past
+constexpr int kBp32UnitMax = 16 * (4 + 4 * 4 * 32);  // 8256: 16 BP32 metablocks at width 32
+static_assert(kBp32UnitMax + 15 + 32 <= kBuf, "a BP32 unit, its 16-byte alignment and the read-past slack fit");
 
 template <int FMT>
 __device__ __forceinline__ uint4 unpack_block(const uint8_t* buf, uint32_t base_bytes, uint32_t bitbase,
@@ -72,6 +74,45 @@ __device__ __forceinline__ bool bp128_unpack_unit(const uint8_t* buf, uint32_t s
             base += 16 * b;
             bitbase += 4 * b;
         }
+    }
+    return true;
+}
+
+// BP32 (Sec. 6.2; R20): checks and unpacks the K metablocks of 128
+// integers staged at `p` (4-byte aligned, `size` bytes).  Metablock k is a
+// descriptor word (byte j = width of 32-integer block j) and blocks of b_j
+// words packed LSB-first in one lane.  Lane t takes integers 4(t%8)..+3 of
+// block t/8, which are integers 4t..4t+3 of the metablock: row ownership,
+// as for the paper layout.  Returns false, with ECORRUPT recorded, if a
+// width exceeds 32 or the widths do not add up to `size`.
+__device__ __forceinline__ bool bp32_unpack_unit(const uint8_t* p, uint32_t size, uint32_t K, uint4 (&v)[16],
+                                                 WsHeader* h, int lane) {
+    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(p);
+    const uint32_t j = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
+    uint32_t off = 0;  // words
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if ((uint32_t)k < K) {
+            const uint32_t desc = off < size / 4 ? w32[off] : 0xFFFFFFFFu;
+            const uint32_t b0 = desc & 255u, b1 = (desc >> 8) & 255u, b2 = (desc >> 16) & 255u, b3 = desc >> 24;
+            bad = bad || b0 > 32 || b1 > 32 || b2 > 32 || b3 > 32;
+            const uint32_t b = bad ? 0u : j == 0 ? b0 : j == 1 ? b1 : j == 2 ? b2 : b3;
+            const uint32_t start = off + 1 + (j > 0 ? b0 : 0u) + (j > 1 ? b1 : 0u) + (j > 2 ? b2 : 0u);
+            const uint32_t mask = width_mask(b);
+            uint32_t r[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t bit = (i0 + c) * b, w = start + (bit >> 5);
+                r[c] = w + 1 < size / 4 + 8 ? __funnelshift_r(w32[w], w32[w + 1], bit & 31) & mask : 0u;
+            }
+            v[k] = make_uint4(r[0], r[1], r[2], r[3]);
+            off += bad ? 0u : 1 + b0 + b1 + b2 + b3;
+        }
+    }
+    if (bad || 4 * off != size) {
+        if (lane == 0) set_error(h, ICX_ECORRUPT);
+        return false;
     }
     return true;
 }

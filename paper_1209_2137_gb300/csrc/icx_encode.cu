@@ -215,6 +215,99 @@ __global__ void vbyte_tail_encode_kernel(const uint32_t* __restrict__ x, size_t 
     *out_bytes = pos;
 }
 
+// ------------------------------------------------------------ BP32
+
+// Widths of the 4 blocks of 32 integers of each 128-integer metablock (Sec.
+// 6.2, R20) as descriptor words (byte j = width of block j), and the size
+// of each unit of 16 metablocks.  Warp per unit; lane t holds integers
+// 4t..4t+3 of a metablock, so the 8 lanes 8j..8j+7 hold block j.
+template <int DELTA>
+__global__ void bp32_sizes_kernel(const uint32_t* __restrict__ x, size_t n, uint32_t* __restrict__ descs,
+                                  uint32_t* __restrict__ sizes) {
+    const int lane = threadIdx.x & 31;
+    const size_t nb = n / 128, M = (nb + 15) / 16;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x / 32);
+    for (size_t m = blockIdx.x * (size_t)(blockDim.x / 32) + (threadIdx.x >> 5); m < M; m += warps) {
+        const size_t K = min((size_t)16, nb - 16 * m);
+        uint32_t size = 0;
+        for (size_t k = 0; k < K; ++k) {
+            const uint4 d = row_deltas<DELTA>(x, 128 * (16 * m + k), lane);
+            uint32_t orv = d.x | d.y | d.z | d.w;
+            orv |= __shfl_xor_sync(FULL, orv, 1);
+            orv |= __shfl_xor_sync(FULL, orv, 2);
+            orv |= __shfl_xor_sync(FULL, orv, 4);
+            const uint32_t b = bitlen32(orv);  // width of the block's largest delta
+            const uint32_t desc = __shfl_sync(FULL, b, 0) | __shfl_sync(FULL, b, 8) << 8 |
+                                  __shfl_sync(FULL, b, 16) << 16 | __shfl_sync(FULL, b, 24) << 24;
+            if (lane == 0) descs[16 * m + k] = desc;
+            size += 4 + 4 * ((desc & 255u) + ((desc >> 8) & 255u) + ((desc >> 16) & 255u) + (desc >> 24));
+        }
+        if (lane == 0) sizes[m] = size;
+    }
+}
+
+// Writes each unit at its offset: per metablock the descriptor word, then
+// the 4 blocks, integer i of block j at bits [i*b_j, (i+1)*b_j) of the
+// block's words (packed in shared memory, stored with 4-byte stores).
+template <int DELTA>
+__global__ void __launch_bounds__(kEncWarps * 32) bp32_pack_kernel(const uint32_t* __restrict__ x, size_t n,
+                                                                   const uint32_t* __restrict__ descs,
+                                                                   const uint64_t* __restrict__ index,
+                                                                   uint8_t* __restrict__ out) {
+    __shared__ uint32_t sm_all[kEncWarps][4 * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* sm = sm_all[warp];
+    const size_t nb = n / 128, M = (nb + 15) / 16;
+    const size_t warps = (size_t)gridDim.x * kEncWarps;
+    const uint32_t j = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
+    for (size_t m = blockIdx.x * (size_t)kEncWarps + warp; m < M; m += warps) {
+        const size_t K = min((size_t)16, nb - 16 * m);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(out + index[m]);  // 4-byte aligned: every size is
+        for (size_t k = 0; k < K; ++k) {
+            const uint32_t desc = descs[16 * m + k];
+            const uint32_t bw[4] = {desc & 255u, (desc >> 8) & 255u, (desc >> 16) & 255u, desc >> 24};
+            const uint32_t b = bw[j];
+            for (int i = lane; i < 128; i += 32) sm[i] = 0;
+            __syncwarp();
+            const uint4 d = row_deltas<DELTA>(x, 128 * (16 * m + k), lane);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t bit = (i0 + c) * b, w = bit >> 5, sh = bit & 31, val = comp(d, c);
+                if (b) {
+                    atomicOr(&sm[32 * j + w], val << sh);
+                    if (sh + b > 32) atomicOr(&sm[32 * j + w + 1], val >> (32 - sh));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) dst[0] = desc;
+            uint32_t o = 1;
+            for (int jj = 0; jj < 4; ++jj) {
+                if ((uint32_t)lane < bw[jj]) dst[o + lane] = sm[32 * jj + lane];
+                o += bw[jj];
+            }
+            __syncwarp();
+            dst += o;
+        }
+    }
+}
+
+template <int DELTA>
+static cudaError_t launch_bp32_encode_t(const uint32_t* x, size_t n, uint8_t* out, uint64_t* index,
+                                        uint64_t* out_bytes, uint32_t* descs, uint32_t* sizes, cudaStream_t s) {
+    const size_t nb = n / 128, M = (nb + 15) / 16;
+    if (M > 0) {
+        const int grid = (int)min((M + 3) / 4, (size_t)152 * 8);
+        bp32_sizes_kernel<DELTA><<<grid, 128, 0, s>>>(x, n, descs, sizes);
+    }
+    scan_sizes_kernel<<<1, 1024, 0, s>>>(sizes, M, index);
+    if (M > 0) {
+        const int grid = (int)min((M + kEncWarps - 1) / kEncWarps, (size_t)152 * 8);
+        bp32_pack_kernel<DELTA><<<grid, kEncWarps * 32, 0, s>>>(x, n, descs, index, out);
+    }
+    vbyte_tail_encode_kernel<DELTA><<<1, 32, 0, s>>>(x, n, index, M, out, out_bytes);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launcher
 
 template <int DELTA, int FMT>
@@ -245,6 +338,13 @@ cudaError_t launch_bp128_encode(int delta, int fmt, const uint32_t* x, size_t n,
     ICX_CASE(ICX_DELTA_1, ICX_FMT_W32)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_W32)
 #undef ICX_CASE
+    uint32_t* descs = reinterpret_cast<uint32_t*>(widths);  // 4-byte aligned workspace region
+    if (fmt == ICX_FMT_BP32 && delta == ICX_DELTA_NONE)
+        return launch_bp32_encode_t<ICX_DELTA_NONE>(x, n, out, index, out_bytes, descs, sizes, s);
+    if (fmt == ICX_FMT_BP32 && delta == ICX_DELTA_1)
+        return launch_bp32_encode_t<ICX_DELTA_1>(x, n, out, index, out_bytes, descs, sizes, s);
+    if (fmt == ICX_FMT_BP32 && delta == ICX_DELTA_4)
+        return launch_bp32_encode_t<ICX_DELTA_4>(x, n, out, index, out_bytes, descs, sizes, s);
     return cudaErrorInvalidValue;
 }
 

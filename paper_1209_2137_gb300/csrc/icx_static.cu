@@ -49,7 +49,7 @@ extern "C" icx_status bp128_decode_static(const uint8_t* d_in, size_t in_bytes, 
                                           icx_delta delta, icx_layout fmt, const uint64_t* d_index,
                                           uint32_t* d_status, icx_stream_t stream) {
     if (!(delta == ICX_DELTA_NONE || delta == ICX_DELTA_1 || delta == ICX_DELTA_4)) return ICX_EINVAL;
-    if (!(fmt == ICX_FMT_PAPER || fmt == ICX_FMT_W32)) return ICX_EINVAL;
+    if (!(fmt == ICX_FMT_PAPER || fmt == ICX_FMT_W32 || fmt == ICX_FMT_BP32)) return ICX_EINVAL;
     if (n > kStaticMaxN) return ICX_ENOSPC;  // beyond the static workspace
     if (n == 0) return ICX_OK;
     if (!d_in || !d_out) return ICX_EINVAL;

@@ -54,6 +54,7 @@ def test_worst_case_streams_fit_max_bytes(lib):
     x = np.full(2048 * 3 + 100, 0xFFFFFFFF, dtype=np.uint32)
     for fmt in (0, 1):
         assert oracle.bp128_encode(x, 0, fmt).size <= icx.bp128_max_bytes(x.size, fmt)
+    assert oracle.bp32_encode(x, 0).size <= icx.bp128_max_bytes(x.size, icx.FMT_BP32)
     assert oracle.fastpfor_encode(x, 0).size <= icx.fastpfor_max_bytes(x.size)
 
 
@@ -73,6 +74,7 @@ def test_plan_create_rejects_bad_lists(lib):
     cases = [
         (icx.ListDesc(16, 64, 32, 128, 48, 7, 1, 0), icx.EINVAL),            # unknown codec
         (icx.ListDesc(16, 64, 32, 128, 48, icx.CODEC_BP128, 2, 0), icx.EINVAL),   # stride 2
+        (icx.ListDesc(16, 64, 32, 128, 48, icx.CODEC_BP128, 1, icx.FMT_BP32), icx.EINVAL),  # BP32 not batched
         (icx.ListDesc(16, 64, 32, 128, 48, icx.CODEC_BP128, 1, 5), icx.EINVAL),   # layout
         (icx.ListDesc(20, 64, 32, 128, 48, icx.CODEC_BP128, 1, 0), icx.EALIGN),   # stream not 16-byte aligned
         (icx.ListDesc(16, 64, 36, 128, 48, icx.CODEC_FASTPFOR, 1, 0), icx.EALIGN),  # output
