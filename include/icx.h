@@ -114,10 +114,11 @@ icx_status icx_status_read(void *d_workspace, icx_stream_t stream, icx_status *o
 
 /* ------------------------------------------------------------- index ---- */
 
-/* Walks the metablocks of a SIMD-BP128 (fmt = PAPER) or W32 stream and writes
- * icx_bp128_index_len(n) byte offsets to d_index: entry m is the offset of
- * metablock m, the last entry the offset of the Variable Byte tail (Sec. 6.2).
- * The walk is sequential (each metablock's size comes from its descriptor). */
+/* Walks the metablocks of a SIMD-BP128 (fmt = PAPER), W32 or BP32 stream and
+ * writes icx_bp128_index_len(n) byte offsets to d_index: entry m is the
+ * offset of metablock m (BP32: of its 16m-th 128-integer metablock), the
+ * last entry the offset of the Variable Byte tail (Sec. 6.2).  The walk is
+ * sequential (each metablock's size comes from its descriptor). */
 icx_status bp128_index(const uint8_t *d_in, size_t in_bytes, size_t n, icx_layout fmt,
                        uint64_t *d_index, void *d_workspace, size_t workspace_bytes,
                        icx_stream_t stream);
@@ -127,7 +128,7 @@ icx_status fastpfor_index(const uint8_t *d_in, size_t in_bytes, size_t n, uint64
 
 /* ------------------------------------------------------------ decode ---- */
 
-/* Decodes n integers from the SIMD-BP128 (or W32) stream d_in[0..in_bytes)
+/* Decodes n integers from the SIMD-BP128 (or W32, or BP32) stream d_in[0..in_bytes)
  * into d_out[0..n): bit unpacking (Sec. 4, Figs. 6-7), the Variable Byte
  * tail (Sec. 2.4) and differential decoding (Sec. 3) in one pass.
  * d_in and d_out must be 16-byte aligned; d_index is the stream's index
@@ -216,8 +217,8 @@ icx_status bp128_decode_static(const uint8_t *d_in, size_t in_bytes, uint32_t *d
 icx_status delta_encode(const uint32_t *d_in, uint32_t *d_out, size_t n, icx_delta delta,
                         icx_stream_t stream);
 
-/* Encodes d_x[0..n) as SIMD-BP128 / W32 (widths are the largest bit length of
- * each block of deltas, Sec. 6.2) into d_out (capacity out_cap bytes, at
+/* Encodes d_x[0..n) as SIMD-BP128 / W32 / BP32 (widths are the largest bit
+ * length of each block of deltas, Sec. 6.2) into d_out (capacity out_cap bytes, at
  * least icx_bp128_max_bytes(n, fmt)), writes the index to d_index and the
  * stream length in bytes to *d_out_bytes (device).  The bytes equal those of
  * the format definition above, bit for bit. */
