@@ -72,6 +72,12 @@ def _load():
             lib.orc_fastpfor_encode.argtypes, lib.orc_fastpfor_encode.restype = [u32p, sz, i, u8p], sz
             lib.orc_fastpfor_decode.argtypes, lib.orc_fastpfor_decode.restype = [u8p, sz, sz, i, u32p], i
             lib.orc_fastpfor_index.argtypes, lib.orc_fastpfor_index.restype = [u8p, sz, sz, u64p], i
+            lib.orc_fastpfor_encode_layout.argtypes = [u32p, sz, i, i, u8p]
+            lib.orc_fastpfor_encode_layout.restype = sz
+            lib.orc_fastpfor_decode_layout.argtypes = [u8p, sz, sz, i, i, u32p]
+            lib.orc_fastpfor_decode_layout.restype = i
+            lib.orc_fastpfor_index_layout.argtypes = [u8p, sz, sz, i, u64p]
+            lib.orc_fastpfor_index_layout.restype = i
             lib.orc_member_bits.argtypes, lib.orc_member_bits.restype = [u32p, sz, u32p, sz, u32p, u64p], None
             lib.orc_bp32_max_bytes.argtypes, lib.orc_bp32_max_bytes.restype = [sz], sz
             lib.orc_bp32_encode.argtypes, lib.orc_bp32_encode.restype = [u32p, sz, i, u8p], sz
@@ -236,41 +242,43 @@ def fastpfor_block_record(values):
     return rec[:r].copy(), high[: nh.value].copy()
 
 
-def fastpfor_encode(x, delta: int) -> np.ndarray:
+def fastpfor_encode(x, delta: int, layout: int = PAPER) -> np.ndarray:
+    """SIMD-FastPFOR (layout PAPER) or the scalar FastPFOR (layout SCALAR)."""
     v = _u32(x)
     lib = _load()
     out = np.zeros(lib.orc_fastpfor_max_bytes(v.size), dtype=np.uint8)
-    n = lib.orc_fastpfor_encode(_ptr(v), v.size, delta, _ptr(out))
+    n = lib.orc_fastpfor_encode_layout(_ptr(v), v.size, delta, layout, _ptr(out))
     return out[:n].copy()
 
 
-def fastpfor_decode(data, n: int, delta: int) -> np.ndarray:
+def fastpfor_decode(data, n: int, delta: int, layout: int = PAPER) -> np.ndarray:
     d = _u8(data)
     out = np.zeros(n, dtype=np.uint32)
-    rc = _load().orc_fastpfor_decode(_ptr(d), d.size, n, delta, _ptr(out))
+    rc = _load().orc_fastpfor_decode_layout(_ptr(d), d.size, n, delta, layout, _ptr(out))
     if rc != 0:
         raise CorruptStream(f"fastpfor stream corrupt (rc={rc})")
     return out
 
 
-def fastpfor_index(data, n: int) -> np.ndarray:
+def fastpfor_index(data, n: int, layout: int = PAPER) -> np.ndarray:
     d = _u8(data)
     lib = _load()
     out = np.zeros(lib.orc_fastpfor_index_len(n), dtype=np.uint64)
-    rc = lib.orc_fastpfor_index(_ptr(d), d.size, n, _ptr(out))
+    rc = lib.orc_fastpfor_index_layout(_ptr(d), d.size, n, layout, _ptr(out))
     if rc != 0:
         raise CorruptStream(f"fastpfor stream corrupt (rc={rc})")
     return out
 
 
 BP32 = 2  # layout value of the BP32 format in the SIMD-BP128 calls
+SCALAR = 2  # the same value: scalar 32-integer packing (BP32 / FastPFOR)
 
 
 def encode(codec: str, x, delta: int, layout: int = PAPER) -> np.ndarray:
     if codec == "bp128":
         return bp32_encode(x, delta) if layout == BP32 else bp128_encode(x, delta, layout)
     if codec == "fastpfor":
-        return fastpfor_encode(x, delta)
+        return fastpfor_encode(x, delta, layout)
     raise ValueError(codec)
 
 
@@ -278,7 +286,7 @@ def decode(codec: str, data, n: int, delta: int, layout: int = PAPER) -> np.ndar
     if codec == "bp128":
         return bp32_decode(data, n, delta) if layout == BP32 else bp128_decode(data, n, delta, layout)
     if codec == "fastpfor":
-        return fastpfor_decode(data, n, delta)
+        return fastpfor_decode(data, n, delta, layout)
     raise ValueError(codec)
 
 
@@ -286,7 +294,7 @@ def index(codec: str, data, n: int, layout: int = PAPER) -> np.ndarray:
     if codec == "bp128":
         return bp32_index(data, n) if layout == BP32 else bp128_index(data, n, layout)
     if codec == "fastpfor":
-        return fastpfor_index(data, n)
+        return fastpfor_index(data, n, layout)
     raise ValueError(codec)
 
 

@@ -364,8 +364,15 @@ static size_t pad_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static uint32_t low_bits(uint32_t v, int b) { return b >= 32 ? v : (v & ((1u << b) - 1u)); }
 
+/* Packing of a page's bit-packed sections (R21): layout 0 = SIMD-FastPFOR
+ * (4 interleaved lanes, exception arrays in chunks of 128), layout 2 =
+ * FastPFOR (one lane: a block's 128 low parts as 4 groups of 32, exception
+ * arrays in groups of 32).  Everything else is shared. */
+static int fp_lanes(int layout) { return layout == 2 ? 1 : 4; }
+static size_t fp_chunk(int layout) { return layout == 2 ? 32 : 128; }
+
 /* Encode `k_count` blocks of 128 values into one page at `out`. */
-static size_t fastpfor_page_encode(const uint32_t *v, size_t k_count, uint8_t *out) {
+static size_t fastpfor_page_encode(const uint32_t *v, size_t k_count, int layout, uint8_t *out) {
     int *b = (int *)malloc(k_count * sizeof(int));
     uint8_t *bytes = (uint8_t *)malloc(k_count * 131 + 4);
     uint32_t *exc[33];
@@ -394,7 +401,7 @@ static size_t fastpfor_page_encode(const uint32_t *v, size_t k_count, uint8_t *o
     uint32_t masked[128];
     for (size_t k = 0; k < k_count; ++k) {
         for (int i = 0; i < 128; ++i) masked[i] = low_bits(v[128 * k + (size_t)i], b[k]);
-        orc_pack(masked, 128, 4, b[k], out + pos);
+        orc_pack(masked, 128, fp_lanes(layout), b[k], out + pos); /* 16 * b bytes either way */
         pos += 16 * (size_t)b[k];
     }
     put_le32(out, (uint32_t)(pos / 4)); /* R5 */
@@ -415,15 +422,16 @@ static size_t fastpfor_page_encode(const uint32_t *v, size_t k_count, uint8_t *o
         size_t aligned = pad_to(pos, 16); /* R9 */
         memset(out + pos, 0, aligned - pos);
         pos = aligned;
-        size_t chunks = (exc_n[dd] + 127) / 128;
+        const size_t chunk = fp_chunk(layout);
+        size_t chunks = (exc_n[dd] + chunk - 1) / chunk;
         for (size_t ch = 0; ch < chunks; ++ch) {
             uint32_t vals[128];
-            for (size_t i = 0; i < 128; ++i) {
-                size_t q = 128 * ch + i;
+            for (size_t i = 0; i < chunk; ++i) {
+                size_t q = chunk * ch + i;
                 vals[i] = q < exc_n[dd] ? exc[dd][q] : 0u;
             }
-            orc_pack(vals, 128, 4, dd, out + pos);
-            pos += 16 * (size_t)dd;
+            orc_pack(vals, chunk, fp_lanes(layout), dd, out + pos);
+            pos += chunk / 8 * (size_t)dd; /* chunk values of dd bits */
         }
     }
     size_t end = pad_to(pos, 16); /* R14 */
@@ -436,7 +444,8 @@ static size_t fastpfor_page_encode(const uint32_t *v, size_t k_count, uint8_t *o
 
 /* Walk one page: fills `v` (k_count*128 values) if v != NULL; returns the page
  * size, or 0 if the page is corrupt or runs past `avail`. */
-static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_count, uint32_t *v) {
+static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_count, int layout, uint32_t *v) {
+    const size_t chunk = fp_chunk(layout);
     if (avail < 16) return 0;
     size_t len_at = 4 * (size_t)get_le32(page);
     if (len_at < 16 || len_at + 4 > avail) return 0;
@@ -454,7 +463,7 @@ static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_c
         if (pos + 4 > avail) return 0;
         arr_n[dd] = get_le32(page + pos);
         pos = pad_to(pos + 4, 16);
-        size_t size = 16 * (size_t)dd * ((arr_n[dd] + 127) / 128);
+        size_t size = chunk / 8 * (size_t)dd * ((arr_n[dd] + chunk - 1) / chunk);
         if (pos + size > avail) return 0;
         arr[dd] = page + pos;
         pos += size;
@@ -468,7 +477,7 @@ static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_c
         r += 2;
         if (b > 32 || maxbits > 32 || maxbits < b) return 0;
         if (packed + 16 * (size_t)b > len_at) return 0;
-        if (v) orc_unpack(page + packed, 128, 4, b, v + 128 * k);
+        if (v) orc_unpack(page + packed, 128, fp_lanes(layout), b, v + 128 * k);
         packed += 16 * (size_t)b;
         if (maxbits > b) {
             if (r + 1 > L) return 0;
@@ -481,9 +490,11 @@ static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_c
                 if (p >= 128) return 0;
                 size_t q = cursor[dd] + e;
                 /* element q of a vertically packed array: chunk q/128, then
-                 * the ordinary 4-lane position inside that chunk. */
-                uint32_t hi = get_field(arr[dd] + 16 * (size_t)dd * (q / 128), 4, (int)(q % 4),
-                                        ((q % 128) / 4) * (size_t)dd, dd);
+                 * the ordinary 4-lane position inside that chunk; of a
+                 * one-lane array: field q of the single bit string. */
+                uint32_t hi = layout == 2 ? get_field(arr[dd], 1, 0, q * (size_t)dd, dd)
+                                          : get_field(arr[dd] + 16 * (size_t)dd * (q / 128), 4, (int)(q % 4),
+                                                      ((q % 128) / 4) * (size_t)dd, dd);
                 if (v) v[128 * k + p] |= hi << b; /* b < 32 here */
             }
             cursor[dd] += c;
@@ -494,24 +505,24 @@ static size_t fastpfor_page_decode(const uint8_t *page, size_t avail, size_t k_c
     return end;
 }
 
-size_t orc_fastpfor_encode(const uint32_t *x, size_t n, int delta, uint8_t *out) {
+size_t orc_fastpfor_encode_layout(const uint32_t *x, size_t n, int delta, int layout, uint8_t *out) {
     uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
     orc_delta_encode(x, n, delta, d);
     size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
     for (size_t p = 0; p < pages; ++p) {
         size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
-        pos += fastpfor_page_encode(d + 65536 * p, k_count, out + pos);
+        pos += fastpfor_page_encode(d + 65536 * p, k_count, layout, out + pos);
     }
     pos += orc_vbyte_encode(d + 128 * nb, n - 128 * nb, out + pos);
     free(d);
     return pos;
 }
 
-int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index) {
+int orc_fastpfor_index_layout(const uint8_t *in, size_t in_bytes, size_t n, int layout, uint64_t *index) {
     size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
     for (size_t p = 0; p < pages; ++p) {
         size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
-        size_t size = fastpfor_page_decode(in + pos, in_bytes - pos, k_count, NULL);
+        size_t size = fastpfor_page_decode(in + pos, in_bytes - pos, k_count, layout, NULL);
         if (size == 0) return ORC_ECORRUPT;
         index[p] = pos;
         pos += size;
@@ -520,13 +531,13 @@ int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *i
     return ORC_OK;
 }
 
-int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x) {
+int orc_fastpfor_decode_layout(const uint8_t *in, size_t in_bytes, size_t n, int delta, int layout, uint32_t *x) {
     uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
     size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
     int rc = ORC_OK;
     for (size_t p = 0; p < pages; ++p) {
         size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
-        size_t size = fastpfor_page_decode(in + pos, in_bytes - pos, k_count, d + 65536 * p);
+        size_t size = fastpfor_page_decode(in + pos, in_bytes - pos, k_count, layout, d + 65536 * p);
         if (size == 0) {
             rc = ORC_ECORRUPT;
             break;
@@ -540,6 +551,18 @@ int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta,
     if (rc == ORC_OK) orc_delta_decode(d, n, delta, x);
     free(d);
     return rc;
+}
+
+size_t orc_fastpfor_encode(const uint32_t *x, size_t n, int delta, uint8_t *out) {
+    return orc_fastpfor_encode_layout(x, n, delta, 0, out);
+}
+
+int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index) {
+    return orc_fastpfor_index_layout(in, in_bytes, n, 0, index);
+}
+
+int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x) {
+    return orc_fastpfor_decode_layout(in, in_bytes, n, delta, 0, x);
 }
 
 /* ------------------------------------------------------- Sec. 6.2: BP32 */

@@ -84,6 +84,14 @@ size_t orc_fastpfor_encode(const uint32_t *x, size_t n, int delta, uint8_t *out)
 int orc_fastpfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x);
 size_t orc_fastpfor_index_len(size_t n);
 int orc_fastpfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
+/* The same with a layout (R21): 0 = SIMD-FastPFOR (the calls above), 2 =
+ * FastPFOR, the paper's scalar variant (Sec. 5): a block's low parts packed
+ * in one lane as 4 groups of 32 integers, each exception array in groups of
+ * 32 (padded to a multiple of 32 values), every other part of the page as
+ * for SIMD-FastPFOR (16-byte aligned sections). */
+size_t orc_fastpfor_encode_layout(const uint32_t *x, size_t n, int delta, int layout, uint8_t *out);
+int orc_fastpfor_decode_layout(const uint8_t *in, size_t in_bytes, size_t n, int delta, int layout, uint32_t *x);
+int orc_fastpfor_index_layout(const uint8_t *in, size_t in_bytes, size_t n, int layout, uint64_t *index);
 
 /* Sec. 6.2, BP32 (the paper's scalar binary packing; R20): n/128 metablocks
  * of 128 integers, each a 32-bit little-endian descriptor (byte j = width

@@ -35,9 +35,11 @@ def bp128_walk(buf, n, layout):
     return metas, pos
 
 
-def fastpfor_walk(buf, n):
+def fastpfor_walk(buf, n, chunk=128):
     """Parses every page; returns (pages, tail offset).  A page is a dict with
-    the per-block records and the exception arrays' counts and offsets."""
+    the per-block records and the exception arrays' counts and offsets.
+    chunk: the padding unit of an exception array (128 values for
+    SIMD-FastPFOR, 32 for the scalar FastPFOR)."""
     buf = bytes(memoryview(buf))
     nb = n // 128
     pages = []
@@ -70,7 +72,7 @@ def fastpfor_walk(buf, n):
                 cnt = le32(buf, q)
                 q = base + pad(q + 4 - base, 16)
                 arrays[d] = (cnt, q)
-                q += 16 * d * ((cnt + 127) // 128)
+                q += chunk // 8 * d * ((cnt + chunk - 1) // chunk)
         end = base + pad(q - base, 16)
         pages.append(dict(offset=base, blocks=k, len_at=len_at, byte_len=L, records=records,
                           bitset=bitset, arrays=arrays, size=end - base))
@@ -96,3 +98,30 @@ def bp32_read(buf, n):
             off += 4 * b
         pos = off
     return metas, deltas, pos
+
+
+def fastpfor_scalar_read(buf, n):
+    """The scalar FastPFOR (Sec. 5, one-lane packing): rebuilds the coded
+    values of every full block from the bytes with Python integers: the low
+    parts as fields i*b of the block's bit string, each exception's high
+    part as field q*d of its array's bit string, OR-ed in at its position."""
+    buf = bytes(memoryview(buf))
+    pages, tail = fastpfor_walk(buf, n, chunk=32)
+    out = []
+    for pg in pages:
+        base = pg["offset"]
+        arrays = {d: int.from_bytes(buf[off:off + 4 * d * ((cnt + 31) // 32)], "little")
+                  for d, (cnt, off) in pg["arrays"].items()}
+        cursor = {d: 0 for d in arrays}
+        packed = base + 16
+        for b, mb, pos_list in pg["records"]:
+            bits = int.from_bytes(buf[packed:packed + 16 * b], "little")
+            vals = [(bits >> (i * b)) & ((1 << b) - 1) for i in range(128)]
+            packed += 16 * b
+            if mb > b:
+                d = mb - b
+                for p in pos_list:
+                    vals[p] |= ((arrays[d] >> (cursor[d] * d)) & ((1 << d) - 1)) << b
+                    cursor[d] += 1
+            out.extend(vals)
+    return pages, out, tail

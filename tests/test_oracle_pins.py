@@ -540,3 +540,45 @@ def test_bp32_corrupt_rejected():
         oracle.bp32_decode(bad, x.size, 1)
     with pytest.raises(oracle.CorruptStream):
         oracle.bp32_decode(enc[:100], x.size, 1)
+
+
+# -- Sec. 5: the scalar FastPFOR (one-lane packing, NEXT-3) ------------------
+
+def test_fastpfor_scalar_bytes_read_back_independently():
+    # the page bytes, read with Python integers, give back the coded values
+    # (the closed-form differences of the input); arrays padded to 32
+    for x in (W.uniform_sorted(65536 * 2 + 128 * 7 + 99, 27, 61), W.exception_heavy(65536 + 128 * 3 + 5, 62)):
+        for delta in (0, 1, 4):
+            if delta and x[1] < x[0]:
+                continue
+            enc = oracle.fastpfor_encode(x, delta, oracle.SCALAR)
+            pages, vals, tail = F.fastpfor_scalar_read(enc, x.size)
+            s = delta if delta else 1
+            xi = [int(v) for v in x]
+            want = [(xi[i] - (xi[i - s] if (delta and i >= s) else 0)) % (1 << 32) for i in range(x.size)]
+            assert vals == want[: 128 * (x.size // 128)], delta
+            for pg in pages:
+                for d, (cnt, off) in pg["arrays"].items():
+                    assert off % 16 == 0 and cnt > 0
+            assert np.array_equal(oracle.fastpfor_decode(enc, x.size, delta, oracle.SCALAR), x)
+            idx = oracle.fastpfor_index(enc, x.size, oracle.SCALAR)
+            assert [int(v) for v in idx[:-1]] == [pg["offset"] for pg in pages] and int(idx[-1]) == tail
+            # the same records as SIMD-FastPFOR: only the bit-packed sections differ
+            simd_pages, _ = F.fastpfor_walk(oracle.fastpfor_encode(x, delta), x.size)
+            assert [pg["records"] for pg in pages] == [pg["records"] for pg in simd_pages]
+
+
+def test_fastpfor_scalar_every_exception_width():
+    # one block per width d = 1..32 with exceptions of exactly d high bits,
+    # counts across the 32-value padding unit
+    for d in range(1, 33):
+        for count in (1, 31, 32, 33):
+            x = np.zeros(128 * 4, np.uint32)
+            for e in range(count):
+                blk, pos = divmod(e, 16)
+                x[128 * blk + 5 * pos + 1] = np.uint32(((1 << (d - 1)) | (e & ((1 << (d - 1)) - 1))) << 0)
+            # widths: the block's low width b = 0 makes every nonzero value an exception of width d
+            enc = oracle.fastpfor_encode(x, 0, oracle.SCALAR)
+            pages, vals, _ = F.fastpfor_scalar_read(enc, x.size)
+            assert vals == [int(v) for v in x]
+            assert np.array_equal(oracle.fastpfor_decode(enc, x.size, 0, oracle.SCALAR), x)
