@@ -459,21 +459,27 @@ def run_exceptions(args, out, ws, flush_l2, world):
 # ------------------------------------------------------------------ BP32 --
 
 def run_bp32(args, arrays, out, ws, flush_l2, world):
-    """BP32 (Sec. 6.2: scalar binary packing of 32-integer blocks, 4 per
-    128-integer metablock) on the long sorted arrays, stride 1 (the paper's
-    differential coding for it) and stride 4."""
+    """The paper's scalar formats on the long sorted arrays: BP32 (Sec. 6.2:
+    binary packing of 32-integer blocks, 4 per 128-integer metablock) and
+    FastPFOR (Sec. 5: SIMD-FastPFOR's pages with one-lane packing), stride 1
+    and stride 4."""
     import torch
 
     import paper_1209_2137_gb300 as icx
 
     peak, _ = peaks()
-    res = {"workload": "the long sorted arrays of the main step, BP32 streams encoded on the GPU", "streams": []}
+    res = {"workload": "the long sorted arrays of the main step, BP32 and FastPFOR streams encoded on the GPU",
+           "streams": []}
     steps = max(3, min(args.steps, 50))
     for name, x in arrays.items():
         xt = torch.from_numpy(x).to(out.device)
         o = out[: x.size]
-        for delta, label in ((icx.DELTA_1, "BP32"), (icx.DELTA_4, "BP32*")):
-            e = icx.bp128_encode(xt, delta, icx.FMT_BP32)
+        for codec, delta, label in (("bp128", icx.DELTA_1, "BP32"), ("bp128", icx.DELTA_4, "BP32*"),
+                                    ("fastpfor", icx.DELTA_1, "FastPFOR"), ("fastpfor", icx.DELTA_4, "FastPFOR*")):
+            if codec == "bp128":
+                e = icx.bp128_encode(xt, delta, icx.FMT_BP32)
+            else:
+                e = icx.fastpfor_encode(xt, delta, fmt=icx.FMT_SCALAR)
             icx.decode(e, out=o, workspace=ws)
             ws.raise_status("BP32 decode")
             if not torch.equal(o, xt):
@@ -497,7 +503,7 @@ def run_bp32(args, arrays, out, ws, flush_l2, world):
                                    "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)})
             del e
         del xt
-    log(f"[bench] BP32: {res['streams']}")
+    log(f"[bench] scalar layouts: {res['streams']}")
     return res
 
 
@@ -787,7 +793,7 @@ def main():
     ap.add_argument("--fastpfor-warps", type=int, default=0, help="warps per CTA of the SIMD-FastPFOR decoder")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
     ap.add_argument("--skip-intersect", action="store_true", help="skip the decode-into-intersection leg")
-    ap.add_argument("--skip-bp32", action="store_true", help="skip the BP32 decodes")
+    ap.add_argument("--skip-bp32", action="store_true", help="skip the scalar-layout (BP32, FastPFOR) decodes")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
     ap.add_argument("--batch-lists", type=int, default=65536)
     ap.add_argument("--batch-total", type=int, default=1 << 28)

@@ -86,7 +86,12 @@ typedef enum { ICX_DELTA_NONE = 0, ICX_DELTA_1 = 1, ICX_DELTA_4 = 4 } icx_delta;
  * blocks of 32 integers packed LSB-first in b_j words; the n % 128 last
  * integers in Variable Byte.  A BP32 index entry marks every 16th metablock
  * (2,048 integers), so the index lengths agree. */
-typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1, ICX_FMT_BP32 = 2 } icx_layout;
+typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1, ICX_FMT_BP32 = 2, ICX_FMT_SCALAR = 2 } icx_layout;
+/* The SIMD-FastPFOR calls take ICX_FMT_PAPER (SIMD-FastPFOR, Sec. 5: 4-lane
+ * vertical packing, exception arrays in chunks of 128) or ICX_FMT_SCALAR
+ * (the paper's scalar FastPFOR: the same pages with a block's low parts
+ * packed in one lane as 4 groups of 32 integers and each exception array
+ * packed in one lane, padded to a multiple of 32 values). */
 
 /* ------------------------------------------------------------- sizes ---- */
 
@@ -122,9 +127,11 @@ icx_status icx_status_read(void *d_workspace, icx_stream_t stream, icx_status *o
 icx_status bp128_index(const uint8_t *d_in, size_t in_bytes, size_t n, icx_layout fmt,
                        uint64_t *d_index, void *d_workspace, size_t workspace_bytes,
                        icx_stream_t stream);
-/* Same for the pages of a SIMD-FastPFOR stream (Sec. 5). */
-icx_status fastpfor_index(const uint8_t *d_in, size_t in_bytes, size_t n, uint64_t *d_index,
-                          void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
+/* Same for the pages of a SIMD-FastPFOR (fmt = PAPER) or FastPFOR (fmt =
+ * SCALAR) stream (Sec. 5). */
+icx_status fastpfor_index(const uint8_t *d_in, size_t in_bytes, size_t n, icx_layout fmt,
+                          uint64_t *d_index, void *d_workspace, size_t workspace_bytes,
+                          icx_stream_t stream);
 
 /* ------------------------------------------------------------ decode ---- */
 
@@ -140,14 +147,14 @@ icx_status bp128_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, s
                         icx_delta delta, icx_layout fmt, const uint64_t *d_index,
                         void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
 
-/* Decodes n integers from the SIMD-FastPFOR stream d_in: per page the
- * exception arrays, the packed low bits of every block, the patch
- * out[p] |= high << b of every exception (Sec. 5), then differential
- * decoding.  d_index may be NULL only when the stream holds at most one page
- * (n < 513*128). */
+/* Decodes n integers from the SIMD-FastPFOR (fmt = PAPER) or FastPFOR (fmt
+ * = SCALAR) stream d_in: per page the exception arrays, the packed low bits
+ * of every block, the patch out[p] |= high << b of every exception (Sec. 5),
+ * then differential decoding.  d_index may be NULL only when the stream
+ * holds at most one page (n < 513*128). */
 icx_status fastpfor_decode(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, size_t n,
-                           icx_delta delta, const uint64_t *d_index, void *d_workspace,
-                           size_t workspace_bytes, icx_stream_t stream);
+                           icx_delta delta, icx_layout fmt, const uint64_t *d_index,
+                           void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
 
 /* Differential decoding alone (Sec. 3): d_out[i] = d_in[i] + d_out[i-s] for
  * s = 1 or 4 (ICX_DELTA_NONE copies).  d_out may equal d_in (in place); the
@@ -227,9 +234,10 @@ icx_status bp128_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_layo
                         uint64_t *d_out_bytes, void *d_encode_workspace,
                         size_t encode_workspace_bytes, icx_stream_t stream);
 
-/* Encodes d_x[0..n) as SIMD-FastPFOR (per block the width minimising
- * 128*b + c*(8 + maxbits - b), ties to the larger b; Sec. 5). */
-icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, uint8_t *d_out,
+/* Encodes d_x[0..n) as SIMD-FastPFOR (fmt = PAPER) or FastPFOR (fmt =
+ * SCALAR): per block the width minimising 128*b + c*(8 + maxbits - b), ties
+ * to the larger b (Sec. 5). */
+icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_layout fmt, uint8_t *d_out,
                            size_t out_cap, uint64_t *d_index, uint64_t *d_out_bytes,
                            void *d_encode_workspace, size_t encode_workspace_bytes,
                            icx_stream_t stream);
@@ -269,8 +277,8 @@ typedef enum { ICX_CODEC_BP128 = 0, ICX_CODEC_FASTPFOR = 1 } icx_codec;
  * output); d_index: its metablock / page index as built by bp128_index,
  * fastpfor_index or the encoders; it may be NULL where the single-array call
  * allows it (at most one metablock / page).  delta: icx_delta; fmt:
- * icx_layout (SIMD-BP128 only: ICX_FMT_PAPER or ICX_FMT_W32, else
- * ICX_EINVAL; ignored for SIMD-FastPFOR).  The caller owns all buffers
+ * icx_layout (SIMD-BP128: ICX_FMT_PAPER or ICX_FMT_W32; SIMD-FastPFOR:
+ * ICX_FMT_PAPER; else ICX_EINVAL).  The caller owns all buffers
  * and keeps them alive and unmodified while the plan is in use. */
 typedef struct {
     const uint8_t *d_in;

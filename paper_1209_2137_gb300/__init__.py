@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "ICX_OK", 1: "ICX_EINVAL", 2: "ICX_EALIGN", 3: "ICX_ECORRUPT"
                 5: "ICX_ECUDA", 6: "ICX_ETIMEOUT"}
 DELTA_NONE, DELTA_1, DELTA_4 = 0, 1, 4
 FMT_PAPER, FMT_W32, FMT_BP32 = 0, 1, 2
+FMT_SCALAR = 2  # the SIMD-FastPFOR calls: the paper's scalar FastPFOR
 CODEC_BP128, CODEC_FASTPFOR = 0, 1
 
 _lock = threading.Lock()
@@ -63,15 +64,15 @@ def lib():
                 "icx_workspace_init": ([vp, sz, vp], i),
                 "icx_status_read": ([vp, vp, ctypes.POINTER(ctypes.c_int)], i),
                 "bp128_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
-                "fastpfor_index": ([vp, sz, sz, vp, vp, sz, vp], i),
+                "fastpfor_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
                 "bp128_decode": ([vp, sz, vp, sz, i, i, vp, vp, sz, vp], i),
-                "fastpfor_decode": ([vp, sz, vp, sz, i, vp, vp, sz, vp], i),
+                "fastpfor_decode": ([vp, sz, vp, sz, i, i, vp, vp, sz, vp], i),
                 "bp128_intersect": ([vp, sz, sz, i, i, vp, vp, sz, vp, vp, vp, sz, vp], i),
                 "sorted_intersect": ([vp, sz, vp, sz, vp, vp, vp], i),
                 "delta_decode": ([vp, vp, sz, i, vp, sz, vp], i),
                 "delta_encode": ([vp, vp, sz, i, vp], i),
                 "bp128_encode": ([vp, sz, i, i, vp, sz, vp, vp, vp, sz, vp], i),
-                "fastpfor_encode": ([vp, sz, i, vp, sz, vp, vp, vp, sz, vp], i),
+                "fastpfor_encode": ([vp, sz, i, i, vp, sz, vp, vp, vp, sz, vp], i),
                 "icx_version": ([], ctypes.c_char_p),
                 "icx_set_tuning": ([ctypes.c_char_p, i], i),
                 "icx_plan_create": ([vp, sz, vp, ctypes.POINTER(vp)], i),
@@ -203,14 +204,14 @@ def bp128_index(data, n: int, fmt: int = FMT_PAPER, index=None, workspace=None, 
     return index
 
 
-def fastpfor_index(data, n: int, index=None, workspace=None, stream=None):
+def fastpfor_index(data, n: int, index=None, workspace=None, stream=None, fmt: int = FMT_PAPER):
     import torch
     _dev(data, torch.uint8, "data")
     if index is None:
         index = torch.empty(fastpfor_index_len(n), dtype=torch.uint64, device=data.device)
     ws = _ws(workspace, n, stream)
-    _check(lib().fastpfor_index(_ptr(data), data.numel(), n, _ptr(index), ws.ptr(), ws.bytes, _stream(stream)),
-           "fastpfor_index")
+    _check(lib().fastpfor_index(_ptr(data), data.numel(), n, fmt, _ptr(index), ws.ptr(), ws.bytes,
+                                _stream(stream)), "fastpfor_index")
     return index
 
 
@@ -232,8 +233,9 @@ def bp128_decode(data, n: int, delta: int = DELTA_1, fmt: int = FMT_PAPER, index
 
 
 def fastpfor_decode(data, n: int, delta: int = DELTA_1, index=None, out=None, workspace=None, stream=None,
-                    in_bytes=None):
-    """Decodes n integers (Sec. 5 pages with exception patching + Sec. 3)."""
+                    in_bytes=None, fmt: int = FMT_PAPER):
+    """Decodes n integers (Sec. 5 pages with exception patching + Sec. 3);
+    fmt FMT_PAPER = SIMD-FastPFOR, FMT_SCALAR = the scalar FastPFOR."""
     import torch
     _dev(data, torch.uint8, "data")
     if out is None:
@@ -241,7 +243,7 @@ def fastpfor_decode(data, n: int, delta: int = DELTA_1, index=None, out=None, wo
     _dev(out, torch.uint32, "out")
     ws = _ws(workspace, n, stream)
     nbytes = data.numel() if in_bytes is None else in_bytes
-    _check(lib().fastpfor_decode(_ptr(data), nbytes, _ptr(out), n, delta, _ptr(index), ws.ptr(), ws.bytes,
+    _check(lib().fastpfor_decode(_ptr(data), nbytes, _ptr(out), n, delta, fmt, _ptr(index), ws.ptr(), ws.bytes,
                                  _stream(stream)), "fastpfor_decode")
     return out
 
@@ -336,8 +338,8 @@ def _encode(codec, x, delta, fmt, stream):
         code = lib().bp128_encode(_ptr(x), n, delta, fmt, _ptr(buf), cap, _ptr(index), _ptr(total), ews.ptr(),
                                   ews.bytes, s)
     else:
-        code = lib().fastpfor_encode(_ptr(x), n, delta, _ptr(buf), cap, _ptr(index), _ptr(total), ews.ptr(),
-                                     ews.bytes, s)
+        code = lib().fastpfor_encode(_ptr(x), n, delta, fmt, _ptr(buf), cap, _ptr(index), _ptr(total),
+                                     ews.ptr(), ews.bytes, s)
     _check(code, f"{codec}_encode")
     ews.raise_status(f"{codec}_encode", stream)
     nbytes = int(total.cpu().view(torch.int64).item())
@@ -351,14 +353,14 @@ def bp128_encode(x, delta: int = DELTA_1, fmt: int = FMT_PAPER, stream=None) -> 
     return _encode("bp128", x, delta, fmt, stream)
 
 
-def fastpfor_encode(x, delta: int = DELTA_1, stream=None) -> Encoded:
-    return _encode("fastpfor", x, delta, FMT_PAPER, stream)
+def fastpfor_encode(x, delta: int = DELTA_1, stream=None, fmt: int = FMT_PAPER) -> Encoded:
+    return _encode("fastpfor", x, delta, fmt, stream)
 
 
 def decode(enc: Encoded, out=None, workspace=None, stream=None):
     if enc.codec == "bp128":
         return bp128_decode(enc.data, enc.n, enc.delta, enc.fmt, enc.index, out, workspace, stream)
-    return fastpfor_decode(enc.data, enc.n, enc.delta, enc.index, out, workspace, stream)
+    return fastpfor_decode(enc.data, enc.n, enc.delta, enc.index, out, workspace, stream, fmt=enc.fmt)
 
 
 def set_tuning(key: str, value: int) -> None:
@@ -503,8 +505,8 @@ class ListPool:
                 code = F.bp128_encode(*args, int(self.deltas[i]), int(fmts[i]), outp, int(cap[i]), idxp, totp,
                                       ews.ptr(), ews.bytes, s)
             else:
-                code = F.fastpfor_encode(*args, int(self.deltas[i]), outp, int(cap[i]), idxp, totp, ews.ptr(),
-                                         ews.bytes, s)
+                code = F.fastpfor_encode(*args, int(self.deltas[i]), FMT_PAPER, outp, int(cap[i]), idxp, totp,
+                                         ews.ptr(), ews.bytes, s)
             _check(code, f"encode list {i}")
         ews.raise_status("pooled encode", stream)
         self.in_bytes = totals.cpu().numpy().view(np.int64).copy()

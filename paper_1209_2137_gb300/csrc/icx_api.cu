@@ -15,6 +15,7 @@ constexpr size_t kMaxN = (size_t)1 << 34;  // bound that keeps every size in ran
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool valid_delta(int d) { return d == ICX_DELTA_NONE || d == ICX_DELTA_1 || d == ICX_DELTA_4; }
 bool valid_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_W32 || f == ICX_FMT_BP32; }
+bool valid_fp_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_SCALAR; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 icx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ICX_OK : ICX_ECUDA; }
@@ -185,19 +186,20 @@ icx_status bp128_encode(const uint32_t* d_x, size_t n, icx_delta delta, icx_layo
                                               (cudaStream_t)stream));
 }
 
-icx_status fastpfor_index(const uint8_t* d_in, size_t in_bytes, size_t n, uint64_t* d_index, void* d_ws,
-                          size_t ws_bytes, icx_stream_t stream) {
-    if (!d_index || !d_ws || n > kMaxN) return ICX_EINVAL;
+icx_status fastpfor_index(const uint8_t* d_in, size_t in_bytes, size_t n, icx_layout fmt, uint64_t* d_index,
+                          void* d_ws, size_t ws_bytes, icx_stream_t stream) {
+    if (!valid_fp_fmt(fmt) || !d_index || !d_ws || n > kMaxN) return ICX_EINVAL;
     if (pages(n) > 0 && !d_in) return ICX_EINVAL;
     if (d_in && !aligned16(d_in)) return ICX_EALIGN;
     if (ws_bytes < icx::kWsHeaderBytes) return ICX_ENOSPC;
-    return from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, d_index, static_cast<WsHeader*>(d_ws),
+    return from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, fmt, d_index, static_cast<WsHeader*>(d_ws),
                                                 (cudaStream_t)stream));
 }
 
 icx_status fastpfor_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, size_t n, icx_delta delta,
-                           const uint64_t* d_index, void* d_ws, size_t ws_bytes, icx_stream_t stream) {
-    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+                           icx_layout fmt, const uint64_t* d_index, void* d_ws, size_t ws_bytes,
+                           icx_stream_t stream) {
+    if (!valid_delta(delta) || !valid_fp_fmt(fmt) || n > kMaxN) return ICX_EINVAL;
     if (n == 0) return ICX_OK;
     if (!d_in || !d_out || !d_ws) return ICX_EINVAL;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws) || (d_index && !aligned16(d_index)))
@@ -207,21 +209,21 @@ icx_status fastpfor_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out
     cudaStream_t s = (cudaStream_t)stream;
     if (!d_index) {
         if (pages(n) > 1) return ICX_EINVAL;
-        const icx_status st = from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, h->mini_index, h, s));
+        const icx_status st = from_cuda(icx::launch_fastpfor_index(d_in, in_bytes, n, fmt, h->mini_index, h, s));
         if (st != ICX_OK) return st;
         d_index = h->mini_index;
     }
-    return from_cuda(icx::launch_fastpfor_decode(delta, d_in, in_bytes, d_out, n, d_index, h, s));
+    return from_cuda(icx::launch_fastpfor_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s));
 }
 
-icx_status fastpfor_encode(const uint32_t* d_x, size_t n, icx_delta delta, uint8_t* d_out, size_t out_cap,
-                           uint64_t* d_index, uint64_t* d_out_bytes, void* d_ews, size_t ews_bytes,
+icx_status fastpfor_encode(const uint32_t* d_x, size_t n, icx_delta delta, icx_layout fmt, uint8_t* d_out,
+                           size_t out_cap, uint64_t* d_index, uint64_t* d_out_bytes, void* d_ews, size_t ews_bytes,
                            icx_stream_t stream) {
-    if (!valid_delta(delta) || n > kMaxN) return ICX_EINVAL;
+    if (!valid_delta(delta) || !valid_fp_fmt(fmt) || n > kMaxN) return ICX_EINVAL;
     if (!d_out || !d_index || !d_out_bytes || !d_ews || (n > 0 && !d_x)) return ICX_EINVAL;
     if ((d_x && !aligned16(d_x)) || !aligned16(d_out)) return ICX_EALIGN;
     if (out_cap < icx_fastpfor_max_bytes(n) || ews_bytes < icx_encode_workspace_bytes(n)) return ICX_ENOSPC;
-    return from_cuda(icx::launch_fastpfor_encode(delta, d_x, n, d_out, out_cap, d_index, d_out_bytes, d_ews,
+    return from_cuda(icx::launch_fastpfor_encode(delta, fmt, d_x, n, d_out, out_cap, d_index, d_out_bytes, d_ews,
                                                  ews_bytes, (cudaStream_t)stream));
 }
 

@@ -541,6 +541,7 @@ icx_status check_list(const icx_list_desc& l) {
     if (!(l.codec == ICX_CODEC_BP128 || l.codec == ICX_CODEC_FASTPFOR)) return ICX_EINVAL;
     if (!(l.delta == ICX_DELTA_NONE || l.delta == ICX_DELTA_1 || l.delta == ICX_DELTA_4)) return ICX_EINVAL;
     if (l.codec == ICX_CODEC_BP128 && !(l.fmt == ICX_FMT_PAPER || l.fmt == ICX_FMT_W32)) return ICX_EINVAL;
+    if (l.codec == ICX_CODEC_FASTPFOR && l.fmt != ICX_FMT_PAPER) return ICX_EINVAL;  // SIMD-FastPFOR only
     if (l.n == 0) return ICX_OK;
     if (!l.d_in || !l.d_out) return ICX_EINVAL;
     if (!aligned16(l.d_in) || !aligned16(l.d_out) || (l.d_index && !aligned16(l.d_index))) return ICX_EALIGN;
@@ -976,7 +977,7 @@ icx_status icx_plan_launch_per_list(icx_plan* p, icx_stream_t stream) {
             if (l.codec == ICX_CODEC_BP128)
                 le = launch_bp128_decode(l.delta, l.fmt, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
             else
-                le = launch_fastpfor_decode(l.delta, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
+                le = launch_fastpfor_decode(l.delta, ICX_FMT_PAPER, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
         }
         cudaError_t e = cudaStreamEndCapture(p->cap, &g);
         if (le != cudaSuccess) e = le;

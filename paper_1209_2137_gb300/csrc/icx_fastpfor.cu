@@ -27,7 +27,7 @@ namespace icx {
 
 // Sequential walk over the pages: each page's size follows from its header
 // word, byte-array length, bitset and exception counts.
-__global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n,
+__global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n, int fmt,
                                       uint64_t* __restrict__ index, WsHeader* h) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
@@ -60,7 +60,8 @@ __global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_
                 break;
             }
             const size_t cnt = ld32(in + q);
-            q = pos + pad_up(q + 4 - pos, 16) + 16 * (size_t)d * ((cnt + 127) / 128);
+            q = pos + pad_up(q + 4 - pos, 16) +
+                (fmt == ICX_FMT_SCALAR ? 4 * (size_t)d * ((cnt + 31) / 32) : 16 * (size_t)d * ((cnt + 127) / 128));
             if (q > in_bytes) bad = true;
         }
         const size_t end = pos + pad_up(q - pos, 16);
@@ -73,15 +74,31 @@ __global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_
 
 // ------------------------------------------------------------ page parse
 
+template <int LAYOUT>
+__device__ __forceinline__ void meta_page(const uint8_t* __restrict__ in, size_t in_bytes, size_t n,
+                                          const uint64_t* __restrict__ index, BlockMeta* __restrict__ meta,
+                                          uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta, WsHeader* h) {
+    __shared__ MetaSmem S;
+    const size_t nb = n / 128, p = blockIdx.x;
+    const uint32_t K = (uint32_t)min((size_t)kBlocksPerPage, nb - kBlocksPerPage * p);
+    parse_page<LAYOUT>(S, in, in_bytes, index[p], index[p + 1], K, meta + kBlocksPerPage * p,
+                       pmeta + kPageMetaWords * p, umeta + kUnitsPerPage * p, h);
+}
+
 __global__ void __launch_bounds__(kMetaThreads, 7)
     fastpfor_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n, const uint64_t* __restrict__ index,
                          BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
                          WsHeader* h) {
-    __shared__ MetaSmem S;
-    const size_t nb = n / 128, p = blockIdx.x;
-    const uint32_t K = (uint32_t)min((size_t)kBlocksPerPage, nb - kBlocksPerPage * p);
-    parse_page(S, in, in_bytes, index[p], index[p + 1], K, meta + kBlocksPerPage * p, pmeta + kPageMetaWords * p,
-               umeta + kUnitsPerPage * p, h);
+    meta_page<ICX_FMT_PAPER>(in, in_bytes, n, index, meta, pmeta, umeta, h);
+}
+
+// The same page parse for the scalar FastPFOR (exception arrays in groups
+// of 32 values).
+__global__ void __launch_bounds__(kMetaThreads, 7)
+    fastpfor_scalar_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n,
+                                const uint64_t* __restrict__ index, BlockMeta* __restrict__ meta,
+                                uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta, WsHeader* h) {
+    meta_page<ICX_FMT_SCALAR>(in, in_bytes, n, index, meta, pmeta, umeta, h);
 }
 
 // ---------------------------------------------------------------- decode
@@ -100,11 +117,13 @@ struct FpSmem {
 // blocks (then the Variable Byte tail), one look-back per tile, exactly like
 // the SIMD-BP128 decoder: per warp its unit's block records, one bulk copy of
 // its packed low bits, unpack, exception patch, local scan.
-template <int DELTA, int W>
-__global__ void __launch_bounds__(W * 32, 16 / W)
-    fastpfor_decode_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
-                           const uint64_t* __restrict__ index, const BlockMeta* __restrict__ meta,
-                           const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, WsHeader* h) {
+template <int DELTA, int W, int LAYOUT>
+__device__ __forceinline__ void fp_decode_units(const uint8_t* __restrict__ in, size_t in_bytes,
+                                                uint32_t* __restrict__ out, size_t n,
+                                                const uint64_t* __restrict__ index,
+                                                const BlockMeta* __restrict__ meta,
+                                                const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta,
+                                                WsHeader* h) {
     static_assert(DELTA != ICX_DELTA_4, "D4 has its own kernel");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     FpSmem<W>& S = *reinterpret_cast<FpSmem<W>*>(smem_raw);
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             }
             if (lane == 0 && pf_a < pf_b && pf_b <= in_bytes && ((pf_a | pf_b) & 15) == 0)
                 prefetch_l2(in + pf_a, (uint32_t)min(pf_b - pf_a, (uint64_t)0x7FFFFFF0u));
-            if (ok) fp_unit_unpack_patch(in, pbase, pg, m, K, buf, blk_of, v, h, lane);
+            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, pg, m, K, buf, blk_of, v, h, lane);
         } else if (u == U) {
             const uint32_t count = (uint32_t)(n - 128 * nb);
             if (count) {
@@ -234,11 +253,13 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
 // loads the next unit's block records and starts its copy before its stores.
 // Measured on the 2^26 sorted arrays it beats the kernel above by 4-5% for
 // D4, but loses 6% for D1, where the register scan of stride 1 spills.
-template <int W>
-__global__ void __launch_bounds__(W * 32, 16 / W)
-    fastpfor_decode_pipe_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out,
-                                size_t n, const uint64_t* __restrict__ index, const BlockMeta* __restrict__ meta,
-                                const uint32_t* __restrict__ pmeta, const uint2* __restrict__ umeta, WsHeader* h) {
+template <int W, int LAYOUT>
+__device__ __forceinline__ void fp_decode_units_pipe(const uint8_t* __restrict__ in, size_t in_bytes,
+                                                     uint32_t* __restrict__ out, size_t n,
+                                                     const uint64_t* __restrict__ index,
+                                                     const BlockMeta* __restrict__ meta,
+                                                     const uint32_t* __restrict__ pmeta,
+                                                     const uint2* __restrict__ umeta, WsHeader* h) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     FpSmem<W>& S = *reinterpret_cast<FpSmem<W>*>(smem_raw);
     uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W>) + 127) / 128) * 128;
@@ -326,7 +347,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             }
             if (lane == 0 && pf_a < pf_b && pf_b <= in_bytes && ((pf_a | pf_b) & 15) == 0)
                 prefetch_l2(in + pf_a, (uint32_t)min(pf_b - pf_a, (uint64_t)0x7FFFFFF0u));
-            if (ok) fp_unit_unpack_patch(in, pbase, S.pg[warp], m, K, buf, blk_of, v, h, lane);
+            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, S.pg[warp], m, K, buf, blk_of, v, h, lane);
         } else if (u == U) {
             const uint32_t count = (uint32_t)(n - 128 * nb);
             if (count) {
@@ -368,21 +389,49 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     finish_launch(h, epoch);
 }
 
+// The kernels: SIMD-FastPFOR, and the scalar FastPFOR under its own names.
+#define ICX_FP_KERNEL_ARGS                                                                                    \
+    const uint8_t *__restrict__ in, size_t in_bytes, uint32_t *__restrict__ out, size_t n,                    \
+        const uint64_t *__restrict__ index, const BlockMeta *__restrict__ meta, const uint32_t *__restrict__ pmeta, \
+        const uint2 *__restrict__ umeta, WsHeader *h
+template <int DELTA, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) fastpfor_decode_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units<DELTA, W, ICX_FMT_PAPER>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
+template <int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) fastpfor_decode_pipe_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units_pipe<W, ICX_FMT_PAPER>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
+template <int DELTA, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) fastpfor_scalar_decode_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units<DELTA, W, ICX_FMT_SCALAR>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
+template <int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) fastpfor_scalar_decode_pipe_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units_pipe<W, ICX_FMT_SCALAR>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
+#undef ICX_FP_KERNEL_ARGS
+
 // ------------------------------------------------------------ launchers
 
-cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, uint64_t* index, WsHeader* h,
-                                  cudaStream_t s) {
-    fastpfor_index_kernel<<<1, 32, 0, s>>>(in, in_bytes, n, index, h);
+cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
+                                  WsHeader* h, cudaStream_t s) {
+    fastpfor_index_kernel<<<1, 32, 0, s>>>(in, in_bytes, n, fmt, index, h);
     return cudaGetLastError();
 }
 
-template <int DELTA, int W>
+template <int DELTA, int W, int LAYOUT>
 static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
                              WsHeader* h, cudaStream_t s) {
     void (*kern)(const uint8_t*, size_t, uint32_t*, size_t, const uint64_t*, const BlockMeta*, const uint32_t*,
                  const uint2*, WsHeader*);
-    if constexpr (DELTA == ICX_DELTA_4)
+    auto meta_kern = LAYOUT == ICX_FMT_SCALAR ? fastpfor_scalar_meta_kernel : fastpfor_meta_kernel;
+    if constexpr (DELTA == ICX_DELTA_4 && LAYOUT == ICX_FMT_SCALAR)
+        kern = fastpfor_scalar_decode_pipe_kernel<W>;
+    else if constexpr (DELTA == ICX_DELTA_4)
         kern = fastpfor_decode_pipe_kernel<W>;
+    else if constexpr (LAYOUT == ICX_FMT_SCALAR)
+        kern = fastpfor_scalar_decode_kernel<DELTA, W>;
     else
         kern = fastpfor_decode_kernel<DELTA, W>;
     const int smem = (int)(((sizeof(FpSmem<W>) + 127) / 128) * 128 + (size_t)W * kFBuf);
@@ -392,7 +441,7 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         // the page parse wants 7 CTAs of 30 KB per SM
-        e = cudaFuncSetAttribute(fastpfor_meta_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(meta_kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         int dev = 0;
@@ -408,7 +457,7 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
     uint2* umeta = reinterpret_cast<uint2*>(ws + ws_unitmeta_off(n));
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, U = (nb + 15) / 16;
     if (P > 0) {
-        fastpfor_meta_kernel<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
+        meta_kern<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
     }
     const size_t ntiles = (U + 1 + W - 1) / W;
     const int grid = (int)min((size_t)blocks_per_sm * sms, ntiles);
@@ -420,19 +469,26 @@ static int g_fp_warps = 0;  // warps per CTA of the SIMD-FastPFOR decoder (0 = d
 
 void set_fastpfor_warps(int w) { g_fp_warps = (w == 4 || w == 8) ? w : 0; }
 
-template <int DELTA>
+template <int DELTA, int LAYOUT>
 static cudaError_t launch_fp_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
                                WsHeader* h, cudaStream_t s) {
     const int w = g_fp_warps ? g_fp_warps : 8;
-    if (w == 4) return launch_fp<DELTA, 4>(in, in_bytes, out, n, index, h, s);
-    return launch_fp<DELTA, 8>(in, in_bytes, out, n, index, h, s);
+    if (w == 4) return launch_fp<DELTA, 4, LAYOUT>(in, in_bytes, out, n, index, h, s);
+    return launch_fp<DELTA, 8, LAYOUT>(in, in_bytes, out, n, index, h, s);
 }
 
-cudaError_t launch_fastpfor_decode(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                    const uint64_t* index, WsHeader* h, cudaStream_t s) {
-    if (delta == ICX_DELTA_1) return launch_fp_w<ICX_DELTA_1>(in, in_bytes, out, n, index, h, s);
-    if (delta == ICX_DELTA_4) return launch_fp_w<ICX_DELTA_4>(in, in_bytes, out, n, index, h, s);
-    return launch_fp_w<ICX_DELTA_NONE>(in, in_bytes, out, n, index, h, s);
+#define ICX_CASE(D, L) \
+    if (delta == D && fmt == L) return launch_fp_w<D, L>(in, in_bytes, out, n, index, h, s);
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_SCALAR)
+#undef ICX_CASE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace icx

@@ -62,11 +62,20 @@ __device__ __forceinline__ uint32_t rec_len_at(const uint32_t* bytes, uint32_t i
     return rec_len(x & 0xFF, (x >> 8) & 0xFF, (x >> 16) & 0xFF);
 }
 
+// Bytes of an exception array of nd values of width d: SIMD-FastPFOR packs
+// chunks of 128 in 4 lanes (16d bytes each), the scalar FastPFOR groups of
+// 32 in one lane (4d bytes each).
+template <int LAYOUT>
+__device__ __forceinline__ uint64_t array_bytes(uint32_t d, uint32_t nd) {
+    return LAYOUT == ICX_FMT_SCALAR ? 4 * (uint64_t)d * ((nd + 31) / 32) : 16 * (uint64_t)d * ((nd + 127) / 128);
+}
+
 // Whole warp: the exception arrays after a page's byte array.  Their offsets
 // follow from the page's per-width counts (lane d-1 holds cnt_total of
 // width d); lane d-1 checks the stored count of array d against it, and the
 // arrays must end exactly at the page end.  Writes the page record pg (array
 // offsets, then the flag word) and returns the warp-uniform `bad`.
+template <int LAYOUT>
 __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize, uint32_t bytes_at, uint32_t Lpad,
                                             uint32_t cnt_total, bool bad, uint32_t* __restrict__ pg, WsHeader* h,
                                             int lane) {
@@ -84,7 +93,7 @@ __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize,
                 my_cnt_at = (uint32_t)q;
                 my_off = (uint32_t)pad_up(q + 4, 16);
             }
-            q = pad_up(q + 4, 16) + 16 * (uint64_t)d * ((nd + 127) / 128);
+            q = pad_up(q + 4, 16) + array_bytes<LAYOUT>(d, nd);
             if (q > psize) {
                 bad = true;
                 break;
@@ -125,6 +134,7 @@ __device__ __forceinline__ uint32_t round_cursor(uint32_t d, uint32_t c, uint32_
 // in[base, end) and holds K blocks; writes the K block records to pm, the
 // exception-array offsets and the page flag to pg, and per unit of 16
 // blocks its packed range to um.
+template <int LAYOUT = ICX_FMT_PAPER>
 __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restrict__ in, size_t in_bytes,
                                            uint64_t base, uint64_t end, uint32_t K, BlockMeta* __restrict__ pm,
                                            uint32_t* __restrict__ pg, uint2* __restrict__ um, WsHeader* h,
@@ -283,7 +293,7 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         }
     }
     // ---- exception arrays (warp 0)
-    if (warp == 0) bad = page_arrays(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
+    if (warp == 0) bad = page_arrays<LAYOUT>(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
     __syncthreads();
     // per unit of 16 blocks: where its packed low bits start and how long they are
     const uint32_t nunits = (K + 15) / 16;
@@ -382,7 +392,7 @@ __device__ __forceinline__ void parse_small_page(SmallPageSmem& S, const uint8_t
         m.flags = 0;
         pm[lane] = m;
     }
-    bad = page_arrays(page, psize, bytes_at, Lpad, cnt, bad, pg, h, lane);
+    bad = page_arrays<ICX_FMT_PAPER>(page, psize, bytes_at, Lpad, cnt, bad, pg, h, lane);
     // per unit of 16 blocks (at most two): its packed range
     const uint32_t k0 = 16 * (uint32_t)(lane & 1), k1 = min(K, k0 + 16) - 1;
     const uint32_t f0 = __shfl_sync(FULL, poff, (int)k0), f1 = __shfl_sync(FULL, poff, (int)(k1 & 31)),
@@ -401,8 +411,11 @@ __device__ __forceinline__ void parse_small_page(SmallPageSmem& S, const uint8_t
 // records in m) and ORs in every exception as high << b (Sec. 5): exception
 // j of block k is element cursor + j of exception array d = maxbits - b of
 // the page (at pbase + pg[d - 1], vertical layout: chunk e/128, lane e%4,
-// field (e%128)/4), its position the j-th byte after pos_off.  The patch rows
-// reuse `buf` once unpacked; blk_of is a kExScratchBytes scratch.
+// field (e%128)/4; scalar FastPFOR: one lane, field e), its position the
+// j-th byte after pos_off.  The scalar layout packs a block's low parts in
+// one lane, 4 groups of 32 integers of b words each.  The patch rows reuse
+// `buf` once unpacked; blk_of is a kExScratchBytes scratch.
+template <int LAYOUT = ICX_FMT_PAPER>
 __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__ in, uint64_t pbase,
                                                      const uint32_t* __restrict__ pg, const BlockMeta* m,
                                                      uint32_t K, uint8_t* buf, uint8_t* blk_of, uint4 (&v)[16],
@@ -413,14 +426,26 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         if ((uint32_t)k < K) {
-            const uint32_t b = m[k].b;
-            const uint32_t bit = (uint32_t)lane * b;
-            const uint4* rows = reinterpret_cast<const uint4*>(buf + (m[k].packed_off - first));
-            const uint4 r0 = rows[bit >> 5], r1 = rows[(bit >> 5) + 1];
-            const uint32_t s = bit & 31, mask = width_mask(b);
-            v[k] = make_uint4(__funnelshift_r(r0.x, r1.x, s) & mask, __funnelshift_r(r0.y, r1.y, s) & mask,
-                              __funnelshift_r(r0.z, r1.z, s) & mask,
-                              __funnelshift_r(r0.w, r1.w, s) & mask);
+            const uint32_t b = m[k].b, mask = width_mask(b);
+            if (LAYOUT == ICX_FMT_SCALAR) {
+                // lane t: fields 4(t%8)..+3 of group t/8 (integers 4t..4t+3)
+                const uint32_t* words = reinterpret_cast<const uint32_t*>(buf + (m[k].packed_off - first));
+                const uint32_t g = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
+                uint32_t r[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t bit = (i0 + c) * b, w = b * g + (bit >> 5);
+                    r[c] = __funnelshift_r(words[w], words[w + 1], bit & 31) & mask;
+                }
+                v[k] = make_uint4(r[0], r[1], r[2], r[3]);
+            } else {
+                const uint32_t bit = (uint32_t)lane * b;
+                const uint4* rows = reinterpret_cast<const uint4*>(buf + (m[k].packed_off - first));
+                const uint4 r0 = rows[bit >> 5], r1 = rows[(bit >> 5) + 1];
+                const uint32_t s = bit & 31;
+                v[k] = make_uint4(__funnelshift_r(r0.x, r1.x, s) & mask, __funnelshift_r(r0.y, r1.y, s) & mask,
+                                  __funnelshift_r(r0.z, r1.z, s) & mask, __funnelshift_r(r0.w, r1.w, s) & mask);
+            }
             C += m[k].c;
         }
     }
@@ -454,15 +479,25 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
                     const BlockMeta mk = m[k];
                     const uint32_t jj = q - pre[k];
                     const uint32_t d = mk.d, e = mk.cursor + jj;
-                    const uint8_t* arr = in + pbase + pg[d - 1] + 16 * (size_t)d * (e >> 7);
-                    const uint32_t ii = e & 127, bit = (ii >> 2) * d;
-                    const uint8_t* wp = arr + 16 * (bit >> 5) + 4 * (ii & 3);
+                    const uint8_t* wp;
+                    uint32_t bit, next;  // next: bytes from a word to the same lane's next word
+                    if (LAYOUT == ICX_FMT_SCALAR) {
+                        bit = e * d;
+                        wp = in + pbase + pg[d - 1] + 4 * (size_t)(bit >> 5);
+                        next = 4;
+                    } else {
+                        const uint8_t* arr = in + pbase + pg[d - 1] + 16 * (size_t)d * (e >> 7);
+                        const uint32_t ii = e & 127;
+                        bit = (ii >> 2) * d;
+                        wp = arr + 16 * (bit >> 5) + 4 * (ii & 3);
+                        next = 16;
+                    }
                     kk[i] = k;
                     sh[i] = bit & 31;
                     dw[i] = d;
                     pos[i] = in[pbase + mk.pos_off + jj];
                     lo[i] = ld32(wp);
-                    hi[i] = (bit & 31) + d > 32 ? ld32(wp + 16) : 0u;
+                    hi[i] = (bit & 31) + d > 32 ? ld32(wp + next) : 0u;
                 }
             }
 #pragma unroll

@@ -94,6 +94,9 @@ __global__ void fp_choose_kernel(const uint32_t* __restrict__ x, size_t n, uint3
 
 // ---------------------------------------------------------------- pass 2
 
+// LAYOUT: ICX_FMT_PAPER = SIMD-FastPFOR (4-lane packing, arrays in chunks of
+// 128), ICX_FMT_SCALAR = FastPFOR (one-lane packing, arrays in groups of 32).
+template <int LAYOUT>
 __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncMeta* __restrict__ meta,
                                  PageEnc* __restrict__ pages, uint32_t* __restrict__ sizes) {
     __shared__ uint32_t cnt_all[4][33];
@@ -145,7 +148,7 @@ __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncM
                 bitset |= 1u << (d - 1);
                 q = (uint32_t)fe_pad(q + 4, 16);
                 pg.arr_off[d - 1] = q;
-                q += 16 * d * ((nd + 127) / 128);
+                q += LAYOUT == ICX_FMT_SCALAR ? 4 * d * ((nd + 31) / 32) : 16 * d * ((nd + 127) / 128);
             }
         }
         pg.bitset = bitset;
@@ -156,7 +159,7 @@ __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncM
 
 // ---------------------------------------------------------------- pass 4
 
-template <int DELTA>
+template <int DELTA, int LAYOUT>
 __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict__ x, size_t n,
                                                       const EncMeta* __restrict__ meta,
                                                       const PageEnc* __restrict__ pages,
@@ -173,16 +176,30 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
         uint8_t* page = out + index[p];
         const uint4 d = fe_row_deltas<DELTA>(x, 128 * k, lane);
         const uint32_t b = m.b, mask = width_mask(b);
-        // packed low b bits, vertical layout (lane t holds field t of the 4 lanes)
+        // packed low b bits: vertical layout (lane t holds field t of the 4
+        // lanes), or one lane (lane t holds fields 4(t%8)..+3 of group t/8,
+        // each group b words)
         for (int i = lane; i < 128; i += 32) sm[i] = 0;
         __syncwarp();
-        const uint32_t bit = (uint32_t)lane * b, w = bit >> 5, s = bit & 31;
+        if (LAYOUT == ICX_FMT_SCALAR) {
+            const uint32_t g = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t val = comp(d, c) & mask;
-            if (b) {
-                atomicOr(&sm[4 * w + c], val << s);
-                if (s + b > 32) atomicOr(&sm[4 * (w + 1) + c], val >> (32 - s));
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t val = comp(d, c) & mask, bit = (i0 + c) * b, w = b * g + (bit >> 5), s = bit & 31;
+                if (b) {
+                    atomicOr(&sm[w], val << s);
+                    if (s + b > 32) atomicOr(&sm[w + 1], val >> (32 - s));
+                }
+            }
+        } else {
+            const uint32_t bit = (uint32_t)lane * b, w = bit >> 5, s = bit & 31;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t val = comp(d, c) & mask;
+                if (b) {
+                    atomicOr(&sm[4 * w + c], val << s);
+                    if (s + b > 32) atomicOr(&sm[4 * (w + 1) + c], val >> (32 - s));
+                }
             }
         }
         __syncwarp();
@@ -222,6 +239,7 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
 
 // ---------------------------------------------------------------- pass 5
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(128) fp_finish_kernel(size_t n, const PageEnc* __restrict__ pages,
                                                         const uint64_t* __restrict__ index, uint8_t* __restrict__ out,
                                                         const uint32_t* __restrict__ scratch) {
@@ -250,6 +268,23 @@ __global__ void __launch_bounds__(128) fp_finish_kernel(size_t n, const PageEnc*
         const uint32_t off = pg.arr_off[d - 1];
         if ((uint32_t)lane < off - (q + 4)) page[q + 4 + lane] = 0;
         const uint32_t* src = scratch + (size_t)kPageExc * p + pg.arr_base[d - 1];
+        if (LAYOUT == ICX_FMT_SCALAR) {
+            // groups of 32 values in one lane: value e of a group at bit e*d
+            const uint32_t groups = (nd + 31) / 32;
+            for (uint32_t gi = 0; gi < groups; ++gi) {
+                for (int i = lane; i < d; i += 32) sm[i] = 0;
+                __syncwarp();
+                const uint32_t e = 32 * gi + lane, val = e < nd ? src[e] : 0u;
+                const uint32_t bit = (uint32_t)lane * d, w = bit >> 5, s = bit & 31;
+                atomicOr(&sm[w], val << s);
+                if (s + d > 32) atomicOr(&sm[w + 1], val >> (32 - s));
+                __syncwarp();
+                if (lane < d) reinterpret_cast<uint32_t*>(page + off + 4 * d * gi)[lane] = sm[lane];
+                __syncwarp();
+            }
+            q = off + 4 * d * groups;
+            continue;
+        }
         const uint32_t chunks = (nd + 127) / 128;
         for (uint32_t ch = 0; ch < chunks; ++ch) {
             for (int i = lane; i < 4 * d; i += 32) sm[i] = 0;
@@ -302,7 +337,7 @@ __global__ void fp_scan_kernel(const uint32_t* __restrict__ sizes, size_t count,
     index[count] = run;
 }
 
-template <int DELTA>
+template <int DELTA, int LAYOUT>
 static cudaError_t fp_encode_t(const uint32_t* x, size_t n, uint8_t* out, uint64_t* index, uint64_t* out_bytes,
                                uint8_t* ws, cudaStream_t s) {
     const FeLayout lay(n);
@@ -315,26 +350,33 @@ static cudaError_t fp_encode_t(const uint32_t* x, size_t n, uint8_t* out, uint64
     if (nb) {
         const int g = (int)min((nb + 3) / 4, (size_t)152 * 16);
         fp_choose_kernel<DELTA><<<g, 128, 0, s>>>(x, n, em);
-        fp_layout_kernel<<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, em, meta, pages, sizes);
+        fp_layout_kernel<LAYOUT><<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, em, meta, pages, sizes);
     }
     fp_scan_kernel<<<1, 32, 0, s>>>(sizes, P, index);
     if (nb) {
         const int g = (int)min((nb + 3) / 4, (size_t)152 * 16);
-        fp_pack_kernel<DELTA><<<g, 128, 0, s>>>(x, n, meta, pages, index, out, scratch);
-        fp_finish_kernel<<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, pages, index, out, scratch);
+        fp_pack_kernel<DELTA, LAYOUT><<<g, 128, 0, s>>>(x, n, meta, pages, index, out, scratch);
+        fp_finish_kernel<LAYOUT><<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, pages, index, out, scratch);
     }
     fp_tail_kernel<DELTA><<<1, 32, 0, s>>>(x, n, index, P, out, out_bytes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fastpfor_encode(int delta, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
+cudaError_t launch_fastpfor_encode(int delta, int fmt, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
                                    uint64_t* index, uint64_t* out_bytes, void* ws, size_t ws_bytes, cudaStream_t s) {
     (void)out_cap;
     if (ws_bytes < FeLayout(n).total) return cudaErrorInvalidValue;
     uint8_t* w = static_cast<uint8_t*>(ws);
-    if (delta == ICX_DELTA_1) return fp_encode_t<ICX_DELTA_1>(x, n, out, index, out_bytes, w, s);
-    if (delta == ICX_DELTA_4) return fp_encode_t<ICX_DELTA_4>(x, n, out, index, out_bytes, w, s);
-    return fp_encode_t<ICX_DELTA_NONE>(x, n, out, index, out_bytes, w, s);
+#define ICX_CASE(D, L) \
+    if (delta == D && fmt == L) return fp_encode_t<D, L>(x, n, out, index, out_bytes, w, s);
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_PAPER)
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_SCALAR)
+#undef ICX_CASE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace icx

@@ -15,11 +15,11 @@ cudaError_t launch_delta_decode(int delta, const uint32_t* in, uint32_t* out, si
 cudaError_t launch_delta_encode(int delta, const uint32_t* x, uint32_t* d, size_t n, cudaStream_t s);
 cudaError_t launch_bp128_encode(int delta, int fmt, const uint32_t* x, size_t n, uint8_t* out, uint64_t* index,
                                 uint64_t* out_bytes, uint8_t* widths, uint32_t* sizes, cudaStream_t s);
-cudaError_t launch_fastpfor_decode(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                    const uint64_t* index, WsHeader* h, cudaStream_t s);
-cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, uint64_t* index, WsHeader* h,
-                                  cudaStream_t s);
-cudaError_t launch_fastpfor_encode(int delta, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
+cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
+                                  WsHeader* h, cudaStream_t s);
+cudaError_t launch_fastpfor_encode(int delta, int fmt, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
                                    uint64_t* index, uint64_t* out_bytes, void* ws, size_t ws_bytes,
                                    cudaStream_t s);
 cudaError_t launch_bp128_member(int delta, int fmt, const uint8_t* in, size_t in_bytes, size_t n,
