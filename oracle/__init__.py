@@ -80,6 +80,12 @@ def _load():
             lib.orc_fastpfor_index_layout.restype = i
             lib.orc_member_bits.argtypes, lib.orc_member_bits.restype = [u32p, sz, u32p, sz, u32p, u64p], None
             lib.orc_bp32_max_bytes.argtypes, lib.orc_bp32_max_bytes.restype = [sz], sz
+            lib.orc_simple8b_encode.argtypes, lib.orc_simple8b_encode.restype = [u32p, sz, u64p], sz
+            lib.orc_simple8b_decode.argtypes, lib.orc_simple8b_decode.restype = [u64p, sz, sz, u32p], i
+            lib.orc_simplepfor_max_bytes.argtypes, lib.orc_simplepfor_max_bytes.restype = [sz], sz
+            lib.orc_simplepfor_encode.argtypes, lib.orc_simplepfor_encode.restype = [u32p, sz, i, u8p], sz
+            lib.orc_simplepfor_decode.argtypes, lib.orc_simplepfor_decode.restype = [u8p, sz, sz, i, u32p], i
+            lib.orc_simplepfor_index.argtypes, lib.orc_simplepfor_index.restype = [u8p, sz, sz, u64p], i
             lib.orc_bp32_encode.argtypes, lib.orc_bp32_encode.restype = [u32p, sz, i, u8p], sz
             lib.orc_bp32_decode.argtypes, lib.orc_bp32_decode.restype = [u8p, sz, sz, i, u32p], i
             lib.orc_bp32_index.argtypes, lib.orc_bp32_index.restype = [u8p, sz, sz, u64p], i
@@ -270,6 +276,51 @@ def fastpfor_index(data, n: int, layout: int = PAPER) -> np.ndarray:
     return out
 
 
+# -- Sec. 2 / Sec. 5: Simple-8b and SimplePFOR --------------------------------
+
+def simple8b_encode(values) -> np.ndarray:
+    v = _u32(values)
+    words = np.zeros(max(1, v.size), dtype=np.uint64)
+    w = _load().orc_simple8b_encode(_ptr(v), v.size, _ptr(words))
+    return words[:w].copy()
+
+
+def simple8b_decode(words, count: int) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    out = np.zeros(max(1, count), dtype=np.uint32)
+    rc = _load().orc_simple8b_decode(_ptr(w), w.size, count, _ptr(out))
+    if rc != 0:
+        raise CorruptStream("simple-8b words do not hold the given count")
+    return out[:count].copy()
+
+
+def simplepfor_encode(x, delta: int) -> np.ndarray:
+    v = _u32(x)
+    lib = _load()
+    out = np.zeros(lib.orc_simplepfor_max_bytes(v.size), dtype=np.uint8)
+    n = lib.orc_simplepfor_encode(_ptr(v), v.size, delta, _ptr(out))
+    return out[:n].copy()
+
+
+def simplepfor_decode(data, n: int, delta: int) -> np.ndarray:
+    d = _u8(data)
+    out = np.zeros(n, dtype=np.uint32)
+    rc = _load().orc_simplepfor_decode(_ptr(d), d.size, n, delta, _ptr(out))
+    if rc != 0:
+        raise CorruptStream(f"simplepfor stream corrupt (rc={rc})")
+    return out
+
+
+def simplepfor_index(data, n: int) -> np.ndarray:
+    d = _u8(data)
+    lib = _load()
+    out = np.zeros(lib.orc_fastpfor_index_len(n), dtype=np.uint64)
+    rc = lib.orc_simplepfor_index(_ptr(d), d.size, n, _ptr(out))
+    if rc != 0:
+        raise CorruptStream(f"simplepfor stream corrupt (rc={rc})")
+    return out
+
+
 BP32 = 2  # layout value of the BP32 format in the SIMD-BP128 calls
 SCALAR = 2  # the same value: scalar 32-integer packing (BP32 / FastPFOR)
 
@@ -279,6 +330,8 @@ def encode(codec: str, x, delta: int, layout: int = PAPER) -> np.ndarray:
         return bp32_encode(x, delta) if layout == BP32 else bp128_encode(x, delta, layout)
     if codec == "fastpfor":
         return fastpfor_encode(x, delta, layout)
+    if codec == "simplepfor":
+        return simplepfor_encode(x, delta)
     raise ValueError(codec)
 
 
@@ -287,6 +340,8 @@ def decode(codec: str, data, n: int, delta: int, layout: int = PAPER) -> np.ndar
         return bp32_decode(data, n, delta) if layout == BP32 else bp128_decode(data, n, delta, layout)
     if codec == "fastpfor":
         return fastpfor_decode(data, n, delta, layout)
+    if codec == "simplepfor":
+        return simplepfor_decode(data, n, delta)
     raise ValueError(codec)
 
 
@@ -295,6 +350,8 @@ def index(codec: str, data, n: int, layout: int = PAPER) -> np.ndarray:
         return bp32_index(data, n) if layout == BP32 else bp128_index(data, n, layout)
     if codec == "fastpfor":
         return fastpfor_index(data, n, layout)
+    if codec == "simplepfor":
+        return simplepfor_index(data, n)
     raise ValueError(codec)
 
 

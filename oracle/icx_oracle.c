@@ -640,6 +640,203 @@ int orc_bp32_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uin
     return rc;
 }
 
+/* ------------------------------------------------- Sec. 2: Simple-8b -- */
+
+static const size_t s8_count[16] = {240, 120, 60, 30, 20, 15, 12, 10, 8, 7, 6, 5, 4, 3, 2, 1};
+static const int s8_bits[16] = {0, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20, 30, 60};
+
+size_t orc_simple8b_encode(const uint32_t *v, size_t count, uint64_t *words) {
+    size_t p = 0, w = 0;
+    while (p < count) {
+        int sel = 15;
+        for (int s = 0; s < 16; ++s) {
+            if (p + s8_count[s] > count) continue; /* R23: the whole count must exist */
+            int ok = 1;
+            for (size_t i = 0; i < s8_count[s] && ok; ++i)
+                if (s8_bits[s] < 32 && (uint64_t)v[p + i] >= ((uint64_t)1 << s8_bits[s])) ok = 0;
+            if (ok) {
+                sel = s;
+                break;
+            }
+        }
+        uint64_t word = (uint64_t)sel << 60;
+        if (sel >= 2)
+            for (size_t i = 0; i < s8_count[sel]; ++i) word |= (uint64_t)v[p + i] << (i * (size_t)s8_bits[sel]);
+        words[w++] = word;
+        p += s8_count[sel];
+    }
+    return w;
+}
+
+int orc_simple8b_decode(const uint64_t *words, size_t nwords, size_t count, uint32_t *out) {
+    size_t p = 0;
+    for (size_t w = 0; w < nwords; ++w) {
+        const int sel = (int)(words[w] >> 60);
+        const size_t c = s8_count[sel];
+        if (p + c > count) return ORC_ECORRUPT;
+        for (size_t i = 0; i < c; ++i) {
+            uint64_t x = sel < 2 ? 0 : (words[w] >> (i * (size_t)s8_bits[sel])) & (((uint64_t)1 << s8_bits[sel]) - 1);
+            if (x >> 32) return ORC_ECORRUPT; /* the stream holds 32-bit integers */
+            out[p + i] = (uint32_t)x;
+        }
+        p += c;
+    }
+    return p == count ? ORC_OK : ORC_ECORRUPT;
+}
+
+/* ------------------------------------------------- Sec. 5: SimplePFOR -- */
+
+size_t orc_simplepfor_max_bytes(size_t n) {
+    size_t nb = n / 128, pages = (nb + 511) / 512;
+    /* per page: header, length, N, W, paddings; per block <= 512 packed
+     * bytes, <= 131 record bytes, <= 128 high parts of one word each */
+    return pages * (16 + 4 + 3 + 8 + 15 + 15) + nb * (512 + 131 + 128 * 8) + (n % 128) * 5 + 16;
+}
+
+static size_t simplepfor_page_encode(const uint32_t *v, size_t k_count, uint8_t *out) {
+    uint8_t *bytes = (uint8_t *)malloc(k_count * 131 + 4);
+    uint32_t *high = (uint32_t *)malloc((k_count * 128 + 1) * sizeof(uint32_t));
+    uint64_t *words = (uint64_t *)malloc((k_count * 128 + 1) * sizeof(uint64_t));
+    int *b = (int *)malloc(k_count * sizeof(int));
+    size_t L = 0, N = 0;
+    for (size_t k = 0; k < k_count; ++k) {
+        size_t nh = 0;
+        size_t r = orc_fastpfor_block_record(v + 128 * k, 128, bytes + L, high + N, &nh);
+        b[k] = bytes[L];
+        L += r;
+        N += nh; /* block order, positions ascending */
+    }
+    size_t pos = 16;
+    memset(out, 0, 16);
+    uint32_t masked[128];
+    for (size_t k = 0; k < k_count; ++k) {
+        for (int i = 0; i < 128; ++i) masked[i] = low_bits(v[128 * k + (size_t)i], b[k]);
+        orc_pack(masked, 128, 1, b[k], out + pos); /* one lane, as the scalar FastPFOR */
+        pos += 16 * (size_t)b[k];
+    }
+    put_le32(out, (uint32_t)(pos / 4)); /* R5 */
+    put_le32(out + pos, (uint32_t)L);   /* R15 */
+    pos += 4;
+    memcpy(out + pos, bytes, L);
+    memset(out + pos + L, 0, pad_to(L, 4) - L);
+    pos += pad_to(L, 4);
+    size_t W = orc_simple8b_encode(high, N, words);
+    put_le32(out + pos, (uint32_t)N);
+    put_le32(out + pos + 4, (uint32_t)W);
+    pos += 8;
+    size_t aligned = pad_to(pos, 16);
+    memset(out + pos, 0, aligned - pos);
+    pos = aligned;
+    for (size_t w = 0; w < W; ++w) {
+        put_le32(out + pos, (uint32_t)words[w]);
+        put_le32(out + pos + 4, (uint32_t)(words[w] >> 32));
+        pos += 8;
+    }
+    size_t end = pad_to(pos, 16); /* R14 */
+    memset(out + pos, 0, end - pos);
+    free(bytes);
+    free(high);
+    free(words);
+    free(b);
+    return end;
+}
+
+/* Walk one SimplePFOR page: fills `v` if v != NULL; returns the page size,
+ * or 0 if it is corrupt or runs past `avail`. */
+static size_t simplepfor_page_decode(const uint8_t *page, size_t avail, size_t k_count, uint32_t *v) {
+    if (avail < 16) return 0;
+    size_t len_at = 4 * (size_t)get_le32(page);
+    if (len_at < 16 || len_at + 4 > avail) return 0;
+    size_t L = get_le32(page + len_at);
+    size_t bytes_at = len_at + 4;
+    if (bytes_at + pad_to(L, 4) + 8 > avail) return 0;
+    const uint8_t *bytes = page + bytes_at;
+    size_t pos = bytes_at + pad_to(L, 4);
+    size_t N = get_le32(page + pos), W = get_le32(page + pos + 4);
+    pos = pad_to(pos + 8, 16);
+    if (W > avail / 8 || pos + 8 * W > avail) return 0;
+    size_t end = pad_to(pos + 8 * W, 16);
+    if (end > avail) return 0;
+    uint32_t *high = (uint32_t *)malloc((N + 1) * sizeof(uint32_t));
+    uint64_t *words = (uint64_t *)malloc((W + 1) * sizeof(uint64_t));
+    for (size_t w = 0; w < W; ++w)
+        words[w] = (uint64_t)get_le32(page + pos + 8 * w) | (uint64_t)get_le32(page + pos + 8 * w + 4) << 32;
+    int bad = orc_simple8b_decode(words, W, N, high) != ORC_OK;
+    size_t packed = 16, r = 0, q = 0;
+    for (size_t k = 0; k < k_count && !bad; ++k) {
+        if (r + 2 > L) { bad = 1; break; }
+        int bb = bytes[r], maxbits = bytes[r + 1];
+        r += 2;
+        if (bb > 32 || maxbits > 32 || maxbits < bb || packed + 16 * (size_t)bb > len_at) { bad = 1; break; }
+        if (v) orc_unpack(page + packed, 128, 1, bb, v + 128 * k);
+        packed += 16 * (size_t)bb;
+        if (maxbits > bb) {
+            if (r + 1 > L) { bad = 1; break; }
+            size_t c = bytes[r++];
+            if (c > 128 || r + c > L || q + c > N) { bad = 1; break; }
+            for (size_t e = 0; e < c; ++e) {
+                size_t p = bytes[r + e];
+                if (p >= 128) { bad = 1; break; }
+                if (v) v[128 * k + p] |= high[q + e] << bb; /* bb < 32 here */
+            }
+            q += c;
+            r += c;
+        }
+    }
+    free(high);
+    free(words);
+    if (bad || packed != len_at || q != N) return 0;
+    return end;
+}
+
+size_t orc_simplepfor_encode(const uint32_t *x, size_t n, int delta, uint8_t *out) {
+    uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    orc_delta_encode(x, n, delta, d);
+    size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
+    for (size_t p = 0; p < pages; ++p) {
+        size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
+        pos += simplepfor_page_encode(d + 65536 * p, k_count, out + pos);
+    }
+    pos += orc_vbyte_encode(d + 128 * nb, n - 128 * nb, out + pos);
+    free(d);
+    return pos;
+}
+
+int orc_simplepfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index) {
+    size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
+    for (size_t p = 0; p < pages; ++p) {
+        size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
+        size_t size = simplepfor_page_decode(in + pos, in_bytes - pos, k_count, NULL);
+        if (size == 0) return ORC_ECORRUPT;
+        index[p] = pos;
+        pos += size;
+    }
+    index[pages] = pos;
+    return ORC_OK;
+}
+
+int orc_simplepfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x) {
+    uint32_t *d = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    size_t nb = n / 128, pages = (nb + 511) / 512, pos = 0;
+    int rc = ORC_OK;
+    for (size_t p = 0; p < pages; ++p) {
+        size_t k_count = nb - 512 * p < 512 ? nb - 512 * p : 512;
+        size_t size = simplepfor_page_decode(in + pos, in_bytes - pos, k_count, d + 65536 * p);
+        if (size == 0) {
+            rc = ORC_ECORRUPT;
+            break;
+        }
+        pos += size;
+    }
+    if (rc == ORC_OK) {
+        size_t used = orc_vbyte_decode(in + pos, in_bytes - pos, n - 128 * nb, d + 128 * nb);
+        if (used == (size_t)-1) rc = ORC_ECORRUPT;
+    }
+    if (rc == ORC_OK) orc_delta_decode(d, n, delta, x);
+    free(d);
+    return rc;
+}
+
 /* ---------------------------------------------------------------- Sec. 7 */
 
 void orc_member_bits(const uint32_t *a, size_t na, const uint32_t *b, size_t nb, uint32_t *bits,

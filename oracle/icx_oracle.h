@@ -105,6 +105,26 @@ size_t orc_bp32_encode(const uint32_t *x, size_t n, int delta, uint8_t *out);
 int orc_bp32_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x);
 int orc_bp32_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
 
+/* Sec. 2 (Table 2), Simple-8b: 64-bit little-endian words, selector s in
+ * bits 60..63 (R22); selectors 0 and 1 stand for 240 and 120 zeros (data
+ * bits zero); selector s >= 2 packs count(s) integers of bits(s) bits, the
+ * i-th at bits [i*b, (i+1)*b).  The encoder is greedy: each word takes the
+ * smallest selector whose count(s) next integers all exist and fit (R23).
+ * encode returns the number of words; decode returns 0 if the words hold
+ * exactly `count` integers (written to out), else ORC_ECORRUPT. */
+size_t orc_simple8b_encode(const uint32_t *v, size_t count, uint64_t *words);
+int orc_simple8b_decode(const uint64_t *words, size_t nwords, size_t count, uint32_t *out);
+
+/* Sec. 5, SimplePFOR (R22): the scalar FastPFOR page (R21) whose exception
+ * high parts, in block order (positions ascending within a block), form one
+ * Simple-8b stream: after the byte array, a word N (high parts), a word W
+ * (Simple-8b words), zero padding to 16 bytes, the W words; the page padded
+ * to 16 bytes.  The index has an entry per page and one for the tail. */
+size_t orc_simplepfor_max_bytes(size_t n);
+size_t orc_simplepfor_encode(const uint32_t *x, size_t n, int delta, uint8_t *out);
+int orc_simplepfor_decode(const uint8_t *in, size_t in_bytes, size_t n, int delta, uint32_t *x);
+int orc_simplepfor_index(const uint8_t *in, size_t in_bytes, size_t n, uint64_t *index);
+
 /* Sec. 7 (decoding fused into its consumer; intersections of sorted
  * arrays): membership of the sorted query list b[0..nb) in the sorted list
  * a[0..na), by the textbook merge of two sorted arrays.  Bit j of

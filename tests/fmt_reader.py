@@ -125,3 +125,59 @@ def fastpfor_scalar_read(buf, n):
                     cursor[d] += 1
             out.extend(vals)
     return pages, out, tail
+
+
+def simple8b_table(path):
+    """(count, bits) per selector from the golden copy of the paper's table."""
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): (int(r[1]), int(r[2])) for r in rows}
+
+
+def simple8b_read(words, table):
+    """Integers of a list of Simple-8b words, selector in bits 60..63."""
+    out, sels = [], []
+    for w in words:
+        w = int(w)
+        sel = w >> 60
+        count, bits = table[sel]
+        sels.append(sel)
+        out.extend(0 if bits == 0 else (w >> (i * bits)) & ((1 << bits) - 1) for i in range(count))
+    return out, sels
+
+
+def simplepfor_read(buf, n, table):
+    """SimplePFOR pages (scalar low parts, one Simple-8b stream of exception
+    high parts per page): rebuilds every full block's coded values."""
+    buf = bytes(memoryview(buf))
+    nb = n // 128
+    out, pages, pos = [], [], 0
+    for p in range((nb + 511) // 512):
+        k = min(512, nb - 512 * p)
+        base = pos
+        len_at = 4 * le32(buf, base)
+        L = le32(buf, base + len_at)
+        rec_at = base + len_at + 4
+        q = rec_at + pad(L, 4)
+        N, W = le32(buf, q), le32(buf, q + 4)
+        woff = base + pad(q + 8 - base, 16)
+        words = [int.from_bytes(buf[woff + 8 * i:woff + 8 * i + 8], "little") for i in range(W)]
+        high, sels = simple8b_read(words, table)
+        assert len(high) == N
+        r, packed, e = 0, base + 16, 0
+        for _ in range(k):
+            b, mb = buf[rec_at + r], buf[rec_at + r + 1]
+            r += 2
+            bits = int.from_bytes(buf[packed:packed + 16 * b], "little")
+            vals = [(bits >> (i * b)) & ((1 << b) - 1) for i in range(128)]
+            packed += 16 * b
+            if mb > b:
+                c = buf[rec_at + r]
+                for j in range(c):
+                    vals[buf[rec_at + r + 1 + j]] |= high[e] << b
+                    e += 1
+                r += 1 + c
+            out.extend(vals)
+        end = base + pad(woff + 8 * W - base, 16)
+        pages.append(dict(offset=base, N=N, W=W, words=words, sels=sels, high=high, size=end - base))
+        pos = end
+    return pages, out, pos

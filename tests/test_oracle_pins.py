@@ -582,3 +582,96 @@ def test_fastpfor_scalar_every_exception_width():
             pages, vals, _ = F.fastpfor_scalar_read(enc, x.size)
             assert vals == [int(v) for v in x]
             assert np.array_equal(oracle.fastpfor_decode(enc, x.size, 0, oracle.SCALAR), x)
+
+
+# -- Sec. 2 / Sec. 5: Simple-8b and SimplePFOR (NEXT-4) ----------------------
+
+S8 = F.simple8b_table(os.path.join(os.path.dirname(__file__), "golden", "simple8b_table.txt"))
+
+
+def _greedy_ok(values, sels):
+    # every word took the smallest selector whose whole count of next values
+    # exists and fits (the paper's greedy rule, R23)
+    p = 0
+    for s in sels:
+        for t in range(s):
+            cnt, bits = S8[t]
+            feasible = p + cnt <= len(values) and all(v < (1 << bits) for v in values[p:p + cnt])
+            assert not feasible, (p, s, t)
+        p += S8[s][0]
+    assert p == len(values)
+
+
+def test_simple8b_table_modes():
+    # for each selector, a run that fits it and no smaller selector is coded
+    # with that selector in one word (32-bit values reach selector 15 only
+    # above 2^30, which the 30-bit selector 14 cannot hold)
+    for s, (cnt, bits) in S8.items():
+        if s == 0:
+            vals = [0] * 240
+        elif s == 1:
+            vals = [0] * 120  # 240 zeros do not exist
+        elif s == 15:
+            vals = [0xFFFFFFFF]
+        else:
+            vals = [(1 << bits) - 1] * cnt
+        words = oracle.simple8b_encode(np.array(vals, np.uint32))
+        got, sels = F.simple8b_read(words, S8)
+        assert got == vals and sels == [s], (s, sels)
+        assert list(oracle.simple8b_decode(words, len(vals))) == vals
+
+
+def test_simple8b_random_streams_greedy_and_exact():
+    rng = np.random.default_rng(17)
+    for t in range(200):
+        n = int(rng.integers(0, 700))
+        kind = t % 4
+        if kind == 0:
+            v = rng.integers(0, 2, n)
+        elif kind == 1:
+            v = (rng.random(n) < 0.05) * rng.integers(0, 1 << 20, n)
+        elif kind == 2:
+            v = rng.integers(0, 1 << int(rng.integers(1, 33)), n, dtype=np.uint64)
+        else:
+            v = np.where(rng.random(n) < 0.5, 0, rng.integers(0, 16, n))
+        v = v.astype(np.uint32)
+        words = oracle.simple8b_encode(v)
+        got, sels = F.simple8b_read(words, S8)
+        assert got == [int(a) for a in v], t
+        _greedy_ok([int(a) for a in v], sels)
+        assert np.array_equal(oracle.simple8b_decode(words, n), v)
+        if words.size:
+            with pytest.raises(oracle.CorruptStream):
+                oracle.simple8b_decode(words, n + 1)
+
+
+def test_simplepfor_bytes_read_back_independently():
+    for x in (W.uniform_sorted(65536 * 2 + 128 * 7 + 99, 27, 81), W.exception_heavy(65536 + 128 * 3 + 5, 82)):
+        for delta in (0, 1, 4):
+            if delta and x[1] < x[0]:
+                continue
+            enc = oracle.simplepfor_encode(x, delta)
+            pages, vals, tail = F.simplepfor_read(enc, x.size, S8)
+            s = delta if delta else 1
+            xi = [int(v) for v in x]
+            want = [(xi[i] - (xi[i - s] if (delta and i >= s) else 0)) % (1 << 32) for i in range(x.size)]
+            assert vals == want[: 128 * (x.size // 128)], delta
+            for pg in pages:
+                _greedy_ok(pg["high"], pg["sels"])
+            assert np.array_equal(oracle.simplepfor_decode(enc, x.size, delta), x)
+            idx = oracle.simplepfor_index(enc, x.size)
+            assert [int(v) for v in idx[:-1]] == [pg["offset"] for pg in pages] and int(idx[-1]) == tail
+            # as many exception high parts as the scalar FastPFOR of the same input has exceptions
+            sc, _ = F.fastpfor_walk(oracle.fastpfor_encode(x, delta, oracle.SCALAR), x.size, chunk=32)
+            assert sum(pg["N"] for pg in pages) == sum(len(r[2]) for p in sc for r in p["records"])
+
+
+def test_simplepfor_corrupt_rejected():
+    x = W.exception_heavy(4096, 83)
+    enc = oracle.simplepfor_encode(x, 0)
+    bad = enc.copy()
+    bad[0:4] = 0xFF
+    with pytest.raises(oracle.CorruptStream):
+        oracle.simplepfor_decode(bad, x.size, 0)
+    with pytest.raises(oracle.CorruptStream):
+        oracle.simplepfor_decode(enc[:-20], x.size, 0)
