@@ -460,26 +460,31 @@ def run_exceptions(args, out, ws, flush_l2, world):
 
 def run_bp32(args, arrays, out, ws, flush_l2, world):
     """The paper's scalar formats on the long sorted arrays: BP32 (Sec. 6.2:
-    binary packing of 32-integer blocks, 4 per 128-integer metablock) and
-    FastPFOR (Sec. 5: SIMD-FastPFOR's pages with one-lane packing), stride 1
-    and stride 4."""
+    binary packing of 32-integer blocks, 4 per 128-integer metablock),
+    FastPFOR (Sec. 5: SIMD-FastPFOR's pages with one-lane packing) and
+    SimplePFOR (its exception high parts as one Simple-8b stream per page),
+    stride 1 and stride 4."""
     import torch
 
     import paper_1209_2137_gb300 as icx
 
     peak, _ = peaks()
-    res = {"workload": "the long sorted arrays of the main step, BP32 and FastPFOR streams encoded on the GPU",
+    res = {"workload": "the long sorted arrays of the main step, BP32, FastPFOR and SimplePFOR streams encoded on "
+                       "the GPU",
            "streams": []}
     steps = max(3, min(args.steps, 50))
     for name, x in arrays.items():
         xt = torch.from_numpy(x).to(out.device)
         o = out[: x.size]
         for codec, delta, label in (("bp128", icx.DELTA_1, "BP32"), ("bp128", icx.DELTA_4, "BP32*"),
-                                    ("fastpfor", icx.DELTA_1, "FastPFOR"), ("fastpfor", icx.DELTA_4, "FastPFOR*")):
+                                    ("fastpfor", icx.DELTA_1, "FastPFOR"), ("fastpfor", icx.DELTA_4, "FastPFOR*"),
+                                    ("simple", icx.DELTA_1, "SimplePFOR"), ("simple", icx.DELTA_4, "SimplePFOR*")):
             if codec == "bp128":
                 e = icx.bp128_encode(xt, delta, icx.FMT_BP32)
-            else:
+            elif codec == "fastpfor":
                 e = icx.fastpfor_encode(xt, delta, fmt=icx.FMT_SCALAR)
+            else:
+                e = icx.fastpfor_encode(xt, delta, fmt=icx.FMT_SIMPLE8B)
             icx.decode(e, out=o, workspace=ws)
             ws.raise_status("BP32 decode")
             if not torch.equal(o, xt):

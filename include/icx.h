@@ -86,12 +86,22 @@ typedef enum { ICX_DELTA_NONE = 0, ICX_DELTA_1 = 1, ICX_DELTA_4 = 4 } icx_delta;
  * blocks of 32 integers packed LSB-first in b_j words; the n % 128 last
  * integers in Variable Byte.  A BP32 index entry marks every 16th metablock
  * (2,048 integers), so the index lengths agree. */
-typedef enum { ICX_FMT_PAPER = 0, ICX_FMT_W32 = 1, ICX_FMT_BP32 = 2, ICX_FMT_SCALAR = 2 } icx_layout;
+typedef enum {
+    ICX_FMT_PAPER = 0,
+    ICX_FMT_W32 = 1,
+    ICX_FMT_BP32 = 2,
+    ICX_FMT_SCALAR = 2,
+    ICX_FMT_SIMPLE8B = 3
+} icx_layout;
 /* The SIMD-FastPFOR calls take ICX_FMT_PAPER (SIMD-FastPFOR, Sec. 5: 4-lane
- * vertical packing, exception arrays in chunks of 128) or ICX_FMT_SCALAR
- * (the paper's scalar FastPFOR: the same pages with a block's low parts
- * packed in one lane as 4 groups of 32 integers and each exception array
- * packed in one lane, padded to a multiple of 32 values). */
+ * vertical packing, exception arrays in chunks of 128), ICX_FMT_SCALAR (the
+ * paper's scalar FastPFOR: the same pages with a block's low parts packed
+ * in one lane as 4 groups of 32 integers and each exception array packed in
+ * one lane, padded to a multiple of 32 values) or ICX_FMT_SIMPLE8B (the
+ * paper's SimplePFOR: the scalar FastPFOR page with the exception arrays
+ * replaced by one Simple-8b stream of the page's exception high parts in
+ * block order -- a word N, a word W, then W 64-bit words from the next
+ * 16-byte boundary; Simple-8b per Table 2, selector in bits 60..63). */
 
 /* ------------------------------------------------------------- sizes ---- */
 

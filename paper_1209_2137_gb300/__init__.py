@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "ICX_OK", 1: "ICX_EINVAL", 2: "ICX_EALIGN", 3: "ICX_ECORRUPT"
 DELTA_NONE, DELTA_1, DELTA_4 = 0, 1, 4
 FMT_PAPER, FMT_W32, FMT_BP32 = 0, 1, 2
 FMT_SCALAR = 2  # the SIMD-FastPFOR calls: the paper's scalar FastPFOR
+FMT_SIMPLE8B = 3  # the SIMD-FastPFOR calls: the paper's SimplePFOR
 CODEC_BP128, CODEC_FASTPFOR = 0, 1
 
 _lock = threading.Lock()

@@ -15,7 +15,7 @@ constexpr size_t kMaxN = (size_t)1 << 34;  // bound that keeps every size in ran
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool valid_delta(int d) { return d == ICX_DELTA_NONE || d == ICX_DELTA_1 || d == ICX_DELTA_4; }
 bool valid_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_W32 || f == ICX_FMT_BP32; }
-bool valid_fp_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_SCALAR; }
+bool valid_fp_fmt(int f) { return f == ICX_FMT_PAPER || f == ICX_FMT_SCALAR || f == ICX_FMT_SIMPLE8B; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 icx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ICX_OK : ICX_ECUDA; }
@@ -44,7 +44,8 @@ size_t icx_bp128_max_bytes(size_t n, icx_layout fmt) {
 
 size_t icx_fastpfor_max_bytes(size_t n) {
     const size_t nb = n / 128, P = pages(n);
-    return P * (16 + 4 + 3 + 4 + 15 + 32 * (4 + 15 + 16 * 32)) + nb * (512 + 131 + 512) + (n % 128) * 5 + 16;
+    // per block the exception high parts take <= 512 bytes in arrays, <= 1,024 as Simple-8b words
+    return P * (16 + 4 + 3 + 4 + 15 + 32 * (4 + 15 + 16 * 32)) + nb * (512 + 131 + 1024) + (n % 128) * 5 + 16;
 }
 
 size_t icx_workspace_bytes(size_t n) { return icx::ws_total_bytes(n); }

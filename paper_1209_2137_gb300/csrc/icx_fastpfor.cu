@@ -51,6 +51,18 @@ __global__ void fastpfor_index_kernel(const uint8_t* __restrict__ in, size_t in_
             bad = true;
             continue;
         }
+        if (fmt == kSimple) {  // N, W, then W Simple-8b words from a 16-byte boundary
+            if (q + 8 > in_bytes) {
+                bad = true;
+                continue;
+            }
+            const size_t W = ld32(in + q + 4);
+            q = pos + pad_up(q + 8 - pos, 16) + 8 * W;
+            const size_t end = pos + pad_up(q - pos, 16);
+            if (end > in_bytes) bad = true;
+            pos = end;
+            continue;
+        }
         const uint32_t bitset = ld32(in + q);
         q += 4;
         for (int d = 1; d <= 32 && !bad; ++d) {
@@ -92,6 +104,14 @@ __global__ void __launch_bounds__(kMetaThreads, 7)
     meta_page<ICX_FMT_PAPER>(in, in_bytes, n, index, meta, pmeta, umeta, h);
 }
 
+// The same page parse for SimplePFOR (one Simple-8b stream of high parts).
+__global__ void __launch_bounds__(kMetaThreads, 7)
+    simplepfor_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n,
+                           const uint64_t* __restrict__ index, BlockMeta* __restrict__ meta,
+                           uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta, WsHeader* h) {
+    meta_page<kSimple>(in, in_bytes, n, index, meta, pmeta, umeta, h);
+}
+
 // The same page parse for the scalar FastPFOR (exception arrays in groups
 // of 32 values).
 __global__ void __launch_bounds__(kMetaThreads, 7)
@@ -104,13 +124,23 @@ __global__ void __launch_bounds__(kMetaThreads, 7)
 // ---------------------------------------------------------------- decode
 
 
-template <int W>
+// The page-record word lane `lane` stages for unit uu: the 32 exception-array
+// offsets, or for SimplePFOR the unit's first word, the words' offset and
+// their count in lanes 0..2.
+template <int LAYOUT>
+__device__ __forceinline__ uint32_t page_slot(uint32_t uu, int lane) {
+    if (LAYOUT != kSimple) return (uint32_t)lane;
+    return lane == 0 ? uu % kUnitsPerPage : lane == 1 ? 33u : lane == 2 ? 34u : 35u;
+}
+
+template <int W, int LAYOUT>
 struct FpSmem {
     TileShared t;
     uint64_t bar[W];
     BlockMeta m[W][16];
     uint32_t pg[W][32];           // the unit's page: offsets of its exception arrays
     uint8_t blk_of[W][kExScratchBytes];  // block of the unit's q-th exception, then its counts
+    uint8_t s8[W][LAYOUT == kSimple ? kS8Scratch : 16];  // SimplePFOR: a window of Simple-8b words
 };
 
 // No delta and D1: a CTA of W warps takes tiles of W consecutive units of 16
@@ -126,8 +156,8 @@ __device__ __forceinline__ void fp_decode_units(const uint8_t* __restrict__ in, 
                                                 WsHeader* h) {
     static_assert(DELTA != ICX_DELTA_4, "D4 has its own kernel");
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    FpSmem<W>& S = *reinterpret_cast<FpSmem<W>*>(smem_raw);
-    uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W>) + 127) / 128) * 128;
+    FpSmem<W, LAYOUT>& S = *reinterpret_cast<FpSmem<W, LAYOUT>*>(smem_raw);
+    uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W, LAYOUT>) + 127) / 128) * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* buf = bufs + (size_t)warp * kFBuf;
     uint32_t* buf32 = reinterpret_cast<uint32_t*>(buf);
@@ -166,7 +196,7 @@ __device__ __forceinline__ void fp_decode_units(const uint8_t* __restrict__ in, 
                 r.bad = pmeta[kPageMetaWords * p + 32];
             }
             if ((uint32_t)lane < K) r.mrec = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
-            r.arr = pmeta[kPageMetaWords * p + lane];
+            r.arr = pmeta[kPageMetaWords * p + page_slot<LAYOUT>(uu, lane)];
         }
     };
     // publishes the records and starts the bulk copy; returns 0 = nothing to
@@ -229,7 +259,7 @@ __device__ __forceinline__ void fp_decode_units(const uint8_t* __restrict__ in, 
             }
             if (lane == 0 && pf_a < pf_b && pf_b <= in_bytes && ((pf_a | pf_b) & 15) == 0)
                 prefetch_l2(in + pf_a, (uint32_t)min(pf_b - pf_a, (uint64_t)0x7FFFFFF0u));
-            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, pg, m, K, buf, blk_of, v, h, lane);
+            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, pg, m, K, buf, blk_of, v, h, lane, S.s8[warp]);
         } else if (u == U) {
             const uint32_t count = (uint32_t)(n - 128 * nb);
             if (count) {
@@ -261,8 +291,8 @@ __device__ __forceinline__ void fp_decode_units_pipe(const uint8_t* __restrict__
                                                      const uint32_t* __restrict__ pmeta,
                                                      const uint2* __restrict__ umeta, WsHeader* h) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    FpSmem<W>& S = *reinterpret_cast<FpSmem<W>*>(smem_raw);
-    uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W>) + 127) / 128) * 128;
+    FpSmem<W, LAYOUT>& S = *reinterpret_cast<FpSmem<W, LAYOUT>*>(smem_raw);
+    uint8_t* bufs = smem_raw + ((sizeof(FpSmem<W, LAYOUT>) + 127) / 128) * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* buf = bufs + (size_t)warp * kFBuf;
     uint32_t* buf32 = reinterpret_cast<uint32_t*>(buf);
@@ -294,7 +324,7 @@ __device__ __forceinline__ void fp_decode_units_pipe(const uint8_t* __restrict__
             uint32_t bad = 0;
             uint64_t pb = 0;
             if ((uint32_t)lane < K) mrec = reinterpret_cast<const uint4*>(meta + 16 * (size_t)uu)[lane];
-            const uint32_t arr = pmeta[kPageMetaWords * p + lane];
+            const uint32_t arr = pmeta[kPageMetaWords * p + page_slot<LAYOUT>(uu, lane)];
             if (lane == 0) {
                 pb = index[p];
                 um = umeta[uu];
@@ -347,7 +377,7 @@ __device__ __forceinline__ void fp_decode_units_pipe(const uint8_t* __restrict__
             }
             if (lane == 0 && pf_a < pf_b && pf_b <= in_bytes && ((pf_a | pf_b) & 15) == 0)
                 prefetch_l2(in + pf_a, (uint32_t)min(pf_b - pf_a, (uint64_t)0x7FFFFFF0u));
-            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, S.pg[warp], m, K, buf, blk_of, v, h, lane);
+            if (ok) fp_unit_unpack_patch<LAYOUT>(in, pbase, S.pg[warp], m, K, buf, blk_of, v, h, lane, S.s8[warp]);
         } else if (u == U) {
             const uint32_t count = (uint32_t)(n - 128 * nb);
             if (count) {
@@ -410,6 +440,14 @@ template <int W>
 __global__ void __launch_bounds__(W * 32, 16 / W) fastpfor_scalar_decode_pipe_kernel(ICX_FP_KERNEL_ARGS) {
     fp_decode_units_pipe<W, ICX_FMT_SCALAR>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
 }
+template <int DELTA, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) simplepfor_decode_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units<DELTA, W, kSimple>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
+template <int W>
+__global__ void __launch_bounds__(W * 32, 16 / W) simplepfor_decode_pipe_kernel(ICX_FP_KERNEL_ARGS) {
+    fp_decode_units_pipe<W, kSimple>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
+}
 #undef ICX_FP_KERNEL_ARGS
 
 // ------------------------------------------------------------ launchers
@@ -425,8 +463,14 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
                              WsHeader* h, cudaStream_t s) {
     void (*kern)(const uint8_t*, size_t, uint32_t*, size_t, const uint64_t*, const BlockMeta*, const uint32_t*,
                  const uint2*, WsHeader*);
-    auto meta_kern = LAYOUT == ICX_FMT_SCALAR ? fastpfor_scalar_meta_kernel : fastpfor_meta_kernel;
-    if constexpr (DELTA == ICX_DELTA_4 && LAYOUT == ICX_FMT_SCALAR)
+    auto meta_kern = LAYOUT == ICX_FMT_SCALAR ? fastpfor_scalar_meta_kernel
+                     : LAYOUT == kSimple      ? simplepfor_meta_kernel
+                                              : fastpfor_meta_kernel;
+    if constexpr (DELTA == ICX_DELTA_4 && LAYOUT == kSimple)
+        kern = simplepfor_decode_pipe_kernel<W>;
+    else if constexpr (LAYOUT == kSimple)
+        kern = simplepfor_decode_kernel<DELTA, W>;
+    else if constexpr (DELTA == ICX_DELTA_4 && LAYOUT == ICX_FMT_SCALAR)
         kern = fastpfor_scalar_decode_pipe_kernel<W>;
     else if constexpr (DELTA == ICX_DELTA_4)
         kern = fastpfor_decode_pipe_kernel<W>;
@@ -434,7 +478,7 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
         kern = fastpfor_scalar_decode_kernel<DELTA, W>;
     else
         kern = fastpfor_decode_kernel<DELTA, W>;
-    const int smem = (int)(((sizeof(FpSmem<W>) + 127) / 128) * 128 + (size_t)W * kFBuf);
+    const int smem = (int)(((sizeof(FpSmem<W, LAYOUT>) + 127) / 128) * 128 + (size_t)W * kFBuf);
     static int blocks_per_sm = -1;
     static int sms = 0;
     if (blocks_per_sm < 0) {
@@ -487,6 +531,9 @@ cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_SCALAR)
     ICX_CASE(ICX_DELTA_1, ICX_FMT_SCALAR)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_NONE, kSimple)
+    ICX_CASE(ICX_DELTA_1, kSimple)
+    ICX_CASE(ICX_DELTA_4, kSimple)
 #undef ICX_CASE
     return cudaErrorInvalidValue;
 }

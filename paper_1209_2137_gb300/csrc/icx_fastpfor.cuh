@@ -50,7 +50,24 @@ struct MetaSmem {
     uint32_t wcnt[kMetaThreads / 32][32];  // per warp, exceptions per width
     uint32_t wpk[kMetaThreads / 32];       // per warp, sum of b
     uint32_t ctl[4];                       // window start, next group, chain state
+    uint32_t uexc[kUnitsPerPage];          // SimplePFOR: per unit, page index of its first exception
+    uint32_t s8[4];                        // SimplePFOR: words offset, word count, chunk carry
 };
+
+// SimplePFOR (Sec. 5): a page's exception high parts form one Simple-8b
+// stream (Table 2: per selector, integers per 64-bit word and their width;
+// the selector in bits 60..63, integer i at bits [i*b, (i+1)*b)).
+constexpr int kSimple = ICX_FMT_SIMPLE8B;  // LAYOUT value of SimplePFOR in these templates
+__device__ __forceinline__ uint32_t s8_count(uint32_t sel) {
+    // 240 120 60 30 20 15 12 10 8 7 6 5 4 3 2 1
+    return sel < 2 ? 240u >> sel : sel < 4 ? 60u >> (sel - 2) : sel < 6 ? 20u - 5u * (sel - 4) :
+           sel < 8 ? 12u - 2u * (sel - 6) : sel <= 15 ? 16u - sel : 0u;
+}
+__device__ __forceinline__ uint32_t s8_bits(uint32_t sel) {
+    // 0 0 1 2 3 4 5 6 7 8 10 12 15 20 30 60
+    return sel < 2 ? 0u : sel < 10 ? sel - 1 : sel == 10 ? 10u : sel == 11 ? 12u : sel == 12 ? 15u :
+           sel == 13 ? 20u : sel == 14 ? 30u : 60u;
+}
 
 __device__ __forceinline__ uint32_t rec_len(uint32_t b, uint32_t mb, uint32_t c) {
     return mb > b ? 3u + min(c, 129u) : 2u;
@@ -109,6 +126,40 @@ __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize,
     return bad;
 }
 
+// Whole warp, SimplePFOR: after the byte array a word N (high parts) and a
+// word W (Simple-8b words), then the words from the next 16-byte boundary to
+// the page end.  Checks N against the records' total (lane 0's cnt_total),
+// the sizes against the page, and writes pg[32] (flag), pg[33] (page offset
+// of the words), pg[34] (W); pg[0..31] (each unit's first word) are filled
+// by the caller.  Returns the warp-uniform `bad`.
+__device__ __forceinline__ bool simple_stream(const uint8_t* page, uint32_t psize, uint32_t bytes_at, uint32_t Lpad,
+                                              uint32_t cnt_total, bool bad, uint32_t* __restrict__ pg,
+                                              uint32_t& woff, uint32_t& W, WsHeader* h, int lane) {
+    woff = 0;
+    W = 0;
+    if (!bad) {
+        const uint64_t q = (uint64_t)bytes_at + Lpad;
+        if (q + 8 > psize) {
+            bad = true;
+        } else {
+            const uint32_t N = ld32(page + q);
+            W = ld32(page + q + 4);
+            woff = (uint32_t)pad_up(q + 8, 16);
+            const uint64_t wend = (uint64_t)woff + 8 * (uint64_t)W;
+            bad = N != __shfl_sync(FULL, cnt_total, 0) || wend > psize || pad_up(wend, 16) != psize;
+        }
+    }
+    bad = __any_sync(FULL, bad);
+    pg[lane] = 0xFFFFFFFFu;
+    if (lane == 0) {
+        pg[32] = bad ? 1u : 0u;
+        pg[33] = bad ? 0u : woff;
+        pg[34] = bad ? 0u : W;
+        if (bad) set_error(h, ICX_ECORRUPT);
+    }
+    return bad;
+}
+
 // Exclusive count, per block, of the earlier exceptions of the same width d
 // within one warp round (lane = block; d = 0: no exceptions), added to
 // `base` = the lane-(d-1) running count before the round; lane d-1 of `cnt`
@@ -160,6 +211,7 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
     const uint32_t* arr = reinterpret_cast<const uint32_t*>(page + bytes_at);  // 4-byte aligned
 
     // ---- record starts, one window of the byte array at a time
+    if (LAYOUT == kSimple && tid < (int)kUnitsPerPage) S.uexc[tid] = 0xFFFFFFFFu;
     if (tid == 0) {
         S.ctl[0] = 0;  // window start
         S.ctl[1] = 0;  // next group
@@ -253,7 +305,8 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         const uint32_t incl = warp_incl_scan(bb, lane);
         pk[i] = run + incl - bb;
         run += __shfl_sync(FULL, incl, 31);
-        const uint32_t within = round_cursor(d, c, cnt, lane);
+        // SimplePFOR: one stream for all widths, so one running count
+        const uint32_t within = round_cursor(LAYOUT == kSimple ? (d ? 1u : 0u) : d, c, cnt, lane);
         b_[i] = bb;
         d_[i] = d;
         c_[i] = c;
@@ -277,7 +330,8 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
             if (k < K) {
                 const uint32_t d = d_[i];
                 uint32_t cbase = 0;
-                for (int w = 0; w < warp; ++w) cbase += S.wcnt[w][d ? d - 1 : 0];
+                const int cls = LAYOUT == kSimple ? 0 : (d ? (int)d - 1 : 0);
+                for (int w = 0; w < warp; ++w) cbase += S.wcnt[w][cls];
                 BlockMeta m;
                 m.packed_off = 16 + 16 * (pk_base + pk[i]);
                 m.pos_off = d ? bytes_at + S.start[k] + 3 : 0u;
@@ -287,14 +341,69 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
                 m.c = (uint8_t)c_[i];
                 m.flags = 0;
                 pm[k] = m;
+                if (LAYOUT == kSimple && c_[i]) atomicMin(&S.uexc[k / 16], m.cursor);
                 if (k % 16 == 0) S.urng[k / 16].x = m.packed_off;
                 if (k % 16 == 15 || k == K - 1) S.urng[k / 16].y = m.packed_off + 16 * b_[i];
             }
         }
     }
     // ---- exception arrays (warp 0)
-    if (warp == 0) bad = page_arrays<LAYOUT>(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
-    __syncthreads();
+    if (LAYOUT == kSimple) {
+        if (warp == 0) {
+            uint32_t woff, W;
+            bad = simple_stream(page, psize, bytes_at, Lpad, cnt_total, bad, pg, woff, W, h, lane);
+            if (lane == 0) {
+                S.s8[0] = woff;
+                S.s8[1] = bad ? 0u : W;
+                S.s8[2] = 0;
+            }
+        }
+        __syncthreads();
+        bad = pg[32] != 0;
+        // each unit's first word: the word whose values cover the unit's
+        // first exception (chunks of kMetaThreads words, a CTA scan of their
+        // counts); its offset in that word goes to the first block's flags
+        const uint32_t woff = S.s8[0], W = S.s8[1];
+        const uint32_t nunits_s = (K + 15) / 16;
+        for (uint32_t cb = 0; cb < W; cb += kMetaThreads) {
+            const uint32_t w = cb + tid;
+            uint32_t cnt_w = 0;
+            if (w < W) {
+                const uint64_t word = *reinterpret_cast<const uint64_t*>(page + woff + 8 * (size_t)w);
+                cnt_w = s8_count((uint32_t)(word >> 60));
+            }
+            const uint32_t incl = warp_incl_scan(cnt_w, lane);
+            if (lane == 31) S.wpk[warp] = incl;
+            __syncthreads();
+            uint32_t start = S.s8[2] + incl - cnt_w;
+            for (int ww = 0; ww < warp; ++ww) start += S.wpk[ww];
+            if (cnt_w) {
+                for (uint32_t u = 0; u < nunits_s; ++u) {
+                    const uint32_t e = S.uexc[u];
+                    if (e >= start && e < start + cnt_w) {
+                        pg[u] = w;
+                        pm[16 * u].flags = (uint8_t)(e - start);
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid == kMetaThreads - 1) {
+                uint32_t tot = 0;
+                for (int ww = 0; ww < kMetaThreads / 32; ++ww) tot += S.wpk[ww];
+                S.s8[2] += tot;
+            }
+            __syncthreads();
+        }
+        if (!bad && tid == 0 && S.s8[2] != cnt_total) {  // the words hold exactly N values
+            pg[32] = 1u;
+            set_error(h, ICX_ECORRUPT);
+        }
+        __syncthreads();
+        bad = pg[32] != 0;
+    } else {
+        if (warp == 0) bad = page_arrays<LAYOUT>(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
+        __syncthreads();
+    }
     // per unit of 16 blocks: where its packed low bits start and how long they are
     const uint32_t nunits = (K + 15) / 16;
     if ((uint32_t)tid < nunits) {
@@ -415,11 +524,20 @@ __device__ __forceinline__ void parse_small_page(SmallPageSmem& S, const uint8_t
 // j-th byte after pos_off.  The scalar layout packs a block's low parts in
 // one lane, 4 groups of 32 integers of b words each.  The patch rows reuse
 // `buf` once unpacked; blk_of is a kExScratchBytes scratch.
+//
+// SimplePFOR (LAYOUT kSimple): scalar low parts; the high parts come from the
+// page's Simple-8b words.  pg[0] is the unit's first word, pg[1] the page
+// offset of the words, pg[2] their count, m[0].flags the offset of the
+// unit's first exception in its first word.  Windows of 32 words (one per
+// lane) are staged in s8 (32 words, then 32 value starts) with a warp scan
+// of their counts; each exception finds its word by a 5-step search.
+constexpr int kS8Scratch = 32 * 8 + 32 * 4;
+
 template <int LAYOUT = ICX_FMT_PAPER>
 __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__ in, uint64_t pbase,
                                                      const uint32_t* __restrict__ pg, const BlockMeta* m,
                                                      uint32_t K, uint8_t* buf, uint8_t* blk_of, uint4 (&v)[16],
-                                                     WsHeader* h, int lane) {
+                                                     WsHeader* h, int lane, uint8_t* s8 = nullptr) {
     uint32_t* buf32 = reinterpret_cast<uint32_t*>(buf);
     const uint32_t first = m[0].packed_off;
     uint32_t C = 0;
@@ -427,7 +545,7 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
     for (int k = 0; k < 16; ++k) {
         if ((uint32_t)k < K) {
             const uint32_t b = m[k].b, mask = width_mask(b);
-            if (LAYOUT == ICX_FMT_SCALAR) {
+            if (LAYOUT == ICX_FMT_SCALAR || LAYOUT == kSimple) {
                 // lane t: fields 4(t%8)..+3 of group t/8 (integers 4t..4t+3)
                 const uint32_t* words = reinterpret_cast<const uint32_t*>(buf + (m[k].packed_off - first));
                 const uint32_t g = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
@@ -466,9 +584,72 @@ __device__ __forceinline__ void fp_unit_unpack_patch(const uint8_t* __restrict__
         }
         __syncwarp();
         bool badpos = false;
+        if (LAYOUT == kSimple) {
+            uint64_t* sw = reinterpret_cast<uint64_t*>(s8);
+            int32_t* ss = reinterpret_cast<int32_t*>(s8 + 32 * 8);
+            const uint64_t* words = reinterpret_cast<const uint64_t*>(in + pbase + pg[1]);
+            const uint32_t W = pg[2];
+            uint32_t wbase = pg[0], q0 = 0;
+            int32_t vbase = -(int32_t)m[0].flags;  // value index of the window's first value
+            bool bad8 = wbase == 0xFFFFFFFFu;
+            while (q0 < C && !bad8) {
+                const uint32_t w = wbase + lane;
+                const bool valid = w < W;
+                const uint64_t word = valid ? words[w] : 0ull;
+                const uint32_t cnt = valid ? s8_count((uint32_t)(word >> 60)) : 0u;
+                const uint32_t incl = warp_incl_scan(cnt, lane);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                __syncwarp();
+                sw[lane] = word;
+                ss[lane] = vbase + (int32_t)(incl - cnt);  // past the last word: the window's end
+                __syncwarp();
+                if (total == 0) {
+                    bad8 = true;
+                    break;
+                }
+                const int32_t wend = vbase + (int32_t)total;
+                const uint32_t qend = wend <= 0 ? 0u : min(C, (uint32_t)wend);
+                for (uint32_t qq = q0; qq < qend; qq += 128) {
+                    uint32_t kk[4], pos[4], hv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t q = qq + 32 * i + lane;
+                        kk[i] = 0xFFu;
+                        if (q < qend) {
+                            uint32_t j = 0;
+#pragma unroll
+                            for (uint32_t st = 16; st; st >>= 1)
+                                if (ss[j + st] <= (int32_t)q) j += st;
+                            const uint64_t wj = sw[j];
+                            const uint32_t sel = (uint32_t)(wj >> 60), b8 = s8_bits(sel);
+                            const uint32_t idx = q - (uint32_t)ss[j];
+                            hv[i] = sel < 2 ? 0u : (uint32_t)((wj >> (idx * b8)) & ((1ull << b8) - 1));
+                            const uint32_t k = blk_of[q];
+                            kk[i] = k;
+                            pos[i] = in[pbase + m[k].pos_off + (q - pre[k])];
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (kk[i] != 0xFFu) {
+                            if (pos[i] < 128)
+                                atomicOr(&buf32[128 * kk[i] + pos[i]], hv[i] << m[kk[i]].b);
+                            else
+                                badpos = true;
+                        }
+                    }
+                }
+                q0 = qend;
+                wbase += 32;
+                vbase = wend;
+                if (q0 < C && wbase >= W) bad8 = true;  // the words ran out
+                __syncwarp();
+            }
+            if (bad8) badpos = true;
+        }
         // four independent exceptions per lane per round, so their
         // loads are in flight together
-        for (uint32_t q0 = 0; q0 < C; q0 += 128) {
+        for (uint32_t q0 = 0; q0 < (LAYOUT == kSimple ? 0u : C); q0 += 128) {
             uint32_t kk[4], pos[4], lo[4], hi[4], sh[4], dw[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {

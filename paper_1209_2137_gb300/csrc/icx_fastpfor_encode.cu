@@ -27,6 +27,7 @@ struct EncMeta {
 
 struct PageEnc {
     uint32_t len_at, L, bitset, size;
+    uint32_t N, W;  // SimplePFOR: exception high parts and Simple-8b words of the page
     uint32_t arr_off[32];  // page-relative offset of array d (d = index + 1)
     uint32_t cnt[32];
     uint32_t arr_base[32];  // first scratch slot of array d
@@ -123,8 +124,10 @@ __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncM
             m.d = (uint8_t)(mb - b);
             m.cursor = 0;
             if (mb > b) {
-                m.cursor = cnt[mb - b];
-                cnt[mb - b] += c;
+                // SimplePFOR: one stream in block order (running count in cnt[32])
+                const uint32_t slot = LAYOUT == ICX_FMT_SIMPLE8B ? 32u : mb - b;
+                m.cursor = cnt[slot];
+                cnt[slot] += c;
                 rec += 3 + c;
             } else {
                 rec += 2;
@@ -135,6 +138,8 @@ __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncM
         PageEnc& pg = pages[p];
         pg.len_at = packed;
         pg.L = rec;
+        pg.N = cnt[32];
+        pg.W = 0;
         uint32_t q = packed + 4 + (uint32_t)fe_pad(rec, 4);
         uint32_t bitset = 0, base = 0;
         q += 4;  // bitset word
@@ -153,13 +158,15 @@ __global__ void fp_layout_kernel(size_t n, const uint32_t* __restrict__ em, EncM
         }
         pg.bitset = bitset;
         pg.size = (uint32_t)fe_pad(q, 16);
-        sizes[p] = pg.size;
+        if (LAYOUT != ICX_FMT_SIMPLE8B) sizes[p] = pg.size;  // SimplePFOR: after its words are counted
     }
 }
 
 // ---------------------------------------------------------------- pass 4
 
-template <int DELTA, int LAYOUT>
+// OUT = false: only the exceptions' high parts into the scratch (SimplePFOR
+// sizes its pages from them before the index exists).
+template <int DELTA, int LAYOUT, bool OUT = true>
 __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict__ x, size_t n,
                                                       const EncMeta* __restrict__ meta,
                                                       const PageEnc* __restrict__ pages,
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
         const size_t p = k / kPageBlocks;
         const EncMeta m = meta[k];
         const PageEnc& pg = pages[p];
-        uint8_t* page = out + index[p];
+        uint8_t* page = OUT ? out + index[p] : nullptr;
         const uint4 d = fe_row_deltas<DELTA>(x, 128 * k, lane);
         const uint32_t b = m.b, mask = width_mask(b);
         // packed low b bits: vertical layout (lane t holds field t of the 4
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
         // each group b words)
         for (int i = lane; i < 128; i += 32) sm[i] = 0;
         __syncwarp();
-        if (LAYOUT == ICX_FMT_SCALAR) {
+        if (LAYOUT == ICX_FMT_SCALAR || LAYOUT == ICX_FMT_SIMPLE8B) {
             const uint32_t g = (uint32_t)lane >> 3, i0 = 4 * ((uint32_t)lane & 7);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -203,12 +210,12 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
             }
         }
         __syncwarp();
-        if ((uint32_t)lane < b)
+        if (OUT && (uint32_t)lane < b)
             reinterpret_cast<uint4*>(page + m.packed_off)[lane] = reinterpret_cast<const uint4*>(sm)[lane];
         __syncwarp();
         // byte-array record: b, maxbits[, c, positions ascending]
-        uint8_t* rec = page + pg.len_at + 4 + m.rec_off;
-        if (lane == 0) {
+        uint8_t* rec = OUT ? page + pg.len_at + 4 + m.rec_off : nullptr;
+        if (OUT && lane == 0) {
             rec[0] = (uint8_t)b;
             rec[1] = m.mb;
             if (m.mb > b) rec[2] = m.c;
@@ -228,12 +235,63 @@ __global__ void __launch_bounds__(128) fp_pack_kernel(const uint32_t* __restrict
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (f[c]) {
-                    rec[3 + rank] = (uint8_t)(4 * lane + c);
+                    if (OUT) rec[3 + rank] = (uint8_t)(4 * lane + c);
                     exc[rank] = comp(d, c) >> b;  // b < maxbits <= 32
                     rank += 1;
                 }
             }
         }
+    }
+}
+
+// ------------------------------------------------- SimplePFOR: Simple-8b
+
+// Simple-8b (Sec. 2, Table 2): integers per 64-bit word and their width, per
+// selector (selector in bits 60..63).
+__device__ __forceinline__ uint32_t fe_s8_count(uint32_t s) {
+    const uint8_t c[16] = {240, 120, 60, 30, 20, 15, 12, 10, 8, 7, 6, 5, 4, 3, 2, 1};
+    return c[s & 15];
+}
+__device__ __forceinline__ uint32_t fe_s8_bits(uint32_t s) {
+    const uint8_t b[16] = {0, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20, 30, 60};
+    return b[s & 15];
+}
+
+// Whole warp: the selector of the word starting at value p of v[0..N): the
+// smallest selector whose count next values all exist and fit (Sec. 2's
+// greedy rule; lane s tests selector s).
+__device__ __forceinline__ uint32_t fe_s8_select(const uint32_t* __restrict__ v, uint32_t N, uint32_t p, int lane) {
+    bool ok = false;
+    if (lane < 16) {
+        const uint32_t cnt = fe_s8_count((uint32_t)lane), b = fe_s8_bits((uint32_t)lane);
+        ok = p + cnt <= N;
+        for (uint32_t i = 0; i < cnt && ok; ++i) ok = b >= 32 || v[p + i] < (1u << b);
+    }
+    return (uint32_t)__ffs(__ballot_sync(FULL, ok)) - 1;  // lane 15 (1 value of 60 bits) always fits
+}
+
+// Per page (one warp): the number of Simple-8b words of its exception high
+// parts, then the page size.
+__global__ void __launch_bounds__(128) s8_size_kernel(size_t n, PageEnc* __restrict__ pages,
+                                                      const uint32_t* __restrict__ scratch,
+                                                      uint32_t* __restrict__ sizes) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t nb = n / 128, P = (nb + kPageBlocks - 1) / kPageBlocks;
+    const size_t p = (size_t)blockIdx.x * 4 + warp;
+    if (p >= P) return;
+    PageEnc& pg = pages[p];
+    const uint32_t* v = scratch + (size_t)kPageExc * p;
+    const uint32_t N = pg.N;
+    uint32_t q = 0, W = 0;
+    while (q < N) {
+        q += fe_s8_count(fe_s8_select(v, N, q, lane));
+        ++W;
+    }
+    if (lane == 0) {
+        const uint32_t words_at = (uint32_t)fe_pad(pg.len_at + 4 + fe_pad(pg.L, 4) + 8, 16);
+        pg.W = W;
+        pg.size = (uint32_t)fe_pad(words_at + 8 * (size_t)W, 16);
+        sizes[p] = pg.size;
     }
 }
 
@@ -259,6 +317,31 @@ __global__ void __launch_bounds__(128) fp_finish_kernel(size_t n, const PageEnc*
     const uint32_t bytes_at = pg.len_at + 4, Lpad = (uint32_t)fe_pad(pg.L, 4);
     if ((uint32_t)lane < Lpad - pg.L) page[bytes_at + pg.L + lane] = 0;
     uint32_t q = bytes_at + Lpad;
+    if (LAYOUT == ICX_FMT_SIMPLE8B) {
+        // N, W, zero padding to 16 bytes, the Simple-8b words, zero padding
+        if (lane == 0) {
+            *reinterpret_cast<uint32_t*>(page + q) = pg.N;
+            *reinterpret_cast<uint32_t*>(page + q + 4) = pg.W;
+        }
+        const uint32_t words_at = (uint32_t)fe_pad(q + 8, 16);
+        if ((uint32_t)lane < words_at - (q + 8)) page[q + 8 + lane] = 0;
+        const uint32_t* v = scratch + (size_t)kPageExc * p;
+        uint64_t* words = reinterpret_cast<uint64_t*>(page + words_at);  // 16-byte aligned
+        uint32_t e = 0;
+        for (uint32_t w = 0; w < pg.W; ++w) {
+            const uint32_t sel = fe_s8_select(v, pg.N, e, lane), cnt = fe_s8_count(sel), b = fe_s8_bits(sel);
+            uint64_t word = 0;
+            if (sel >= 2)
+                for (uint32_t i = lane; i < cnt; i += 32) word |= (uint64_t)v[e + i] << (i * b);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) word |= __shfl_xor_sync(FULL, word, o);
+            if (lane == 0) words[w] = word | (uint64_t)sel << 60;
+            e += cnt;
+        }
+        const uint32_t end = words_at + 8 * pg.W;
+        if ((uint32_t)lane < pg.size - end) page[end + lane] = 0;
+        return;
+    }
     if (lane == 0) *reinterpret_cast<uint32_t*>(page + q) = pg.bitset;
     q += 4;
     for (int d = 1; d <= 32; ++d) {
@@ -351,6 +434,10 @@ static cudaError_t fp_encode_t(const uint32_t* x, size_t n, uint8_t* out, uint64
         const int g = (int)min((nb + 3) / 4, (size_t)152 * 16);
         fp_choose_kernel<DELTA><<<g, 128, 0, s>>>(x, n, em);
         fp_layout_kernel<LAYOUT><<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, em, meta, pages, sizes);
+        if (LAYOUT == ICX_FMT_SIMPLE8B) {  // the high parts first: they size the pages
+            fp_pack_kernel<DELTA, LAYOUT, false><<<g, 128, 0, s>>>(x, n, meta, pages, index, out, scratch);
+            s8_size_kernel<<<(unsigned)((P + 3) / 4), 128, 0, s>>>(n, pages, scratch, sizes);
+        }
     }
     fp_scan_kernel<<<1, 32, 0, s>>>(sizes, P, index);
     if (nb) {
@@ -375,6 +462,9 @@ cudaError_t launch_fastpfor_encode(int delta, int fmt, const uint32_t* x, size_t
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_SCALAR)
     ICX_CASE(ICX_DELTA_1, ICX_FMT_SCALAR)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_SCALAR)
+    ICX_CASE(ICX_DELTA_NONE, ICX_FMT_SIMPLE8B)
+    ICX_CASE(ICX_DELTA_1, ICX_FMT_SIMPLE8B)
+    ICX_CASE(ICX_DELTA_4, ICX_FMT_SIMPLE8B)
 #undef ICX_CASE
     return cudaErrorInvalidValue;
 }
