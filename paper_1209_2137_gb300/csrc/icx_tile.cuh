@@ -264,7 +264,9 @@ __device__ __forceinline__ void store_unit(uint32_t* __restrict__ out, size_t fi
             const size_t p = first + 128 * (size_t)k + 4 * (size_t)lane;
             const uint4 r = add4(v[k], pref);
             if (p + 4 <= n) {
-                *reinterpret_cast<uint4*>(out + p) = r;
+                // streaming (evict-first): the output passes through L2 without
+                // pushing out the input prefetched there one grid ahead
+                __stcs(reinterpret_cast<uint4*>(out + p), r);
             } else {
                 for (int c = 0; c < 4; ++c)
                     if (p + c < n) out[p + c] = comp(r, c);
