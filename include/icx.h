@@ -258,7 +258,7 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *   "bp128.l2_prefetch" = 1 (default) / 0: each warp prefetches into L2 the
  *       metablock one grid of tiles ahead;
  *   "fastpfor.warps_per_cta" = 4 or 8 warps per CTA tile of the
- *       SIMD-FastPFOR decoder (0 = default: 4 for stride 4, 8 otherwise).
+ *       SIMD-FastPFOR decoder (0 = default: 4 for SIMD-FastPFOR stride 4, 8 otherwise).
  * Takes effect for later launches; not thread safe against concurrent
  * launches.  ICX_EINVAL for an unknown key. */
 icx_status icx_set_tuning(const char *key, int value);

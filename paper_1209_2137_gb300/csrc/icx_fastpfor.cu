@@ -517,9 +517,10 @@ template <int DELTA, int LAYOUT>
 static cudaError_t launch_fp_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
                                WsHeader* h, cudaStream_t s) {
     // measured on the 2^26 sorted arrays: 4 warps per CTA for the pipelined
-    // stride-4 kernel (0.1816 vs 0.1820 ms), 8 for the others (stride 1:
-    // 0.178 vs 0.181 ms)
-    const int w = g_fp_warps ? g_fp_warps : (DELTA == ICX_DELTA_4 ? 4 : 8);
+    // SIMD-FastPFOR stride-4 kernel (0.1816 vs 0.1820 ms), 8 for the others
+    // (SIMD stride 1: 0.178 vs 0.181 ms; scalar FastPFOR and SimplePFOR
+    // stride 4: 0.183 vs 0.198 and 0.197 vs 0.207 ms)
+    const int w = g_fp_warps ? g_fp_warps : (DELTA == ICX_DELTA_4 && LAYOUT == ICX_FMT_PAPER ? 4 : 8);
     if (w == 4) return launch_fp<DELTA, 4, LAYOUT>(in, in_bytes, out, n, index, h, s);
     return launch_fp<DELTA, 8, LAYOUT>(in, in_bytes, out, n, index, h, s);
 }
