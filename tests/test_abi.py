@@ -99,3 +99,34 @@ def test_tuning_keys(lib):
     with pytest.raises(icx.IcxError) as e:
         icx.set_tuning("no.such.key", 1)
     assert e.value.code == icx.EINVAL
+
+
+def test_layout_and_consumer_argument_checks(lib):
+    # host-side refusals that return before any device call
+    import ctypes
+
+    import paper_1209_2137_gb300 as icx
+    L = icx.lib()
+    vp = ctypes.c_void_p
+    a16, a4 = vp(4096), vp(4100)  # a 16-byte aligned and a 4-byte aligned fake device address
+    # SIMD-FastPFOR calls: W32 is not a FastPFOR layout; SCALAR and SIMPLE8B are
+    assert L.fastpfor_decode(a16, 64, a16, 128, icx.DELTA_1, icx.FMT_W32, None, a16, 1 << 20, None) == icx.EINVAL
+    assert L.fastpfor_index(a16, 64, 128, 7, a16, a16, 1 << 20, None) == icx.EINVAL
+    assert L.fastpfor_encode(a16, 128, icx.DELTA_1, icx.FMT_W32, a16, 1 << 20, a16, a16, a16, 1 << 20,
+                             None) == icx.EINVAL
+    for fmt in (icx.FMT_PAPER, icx.FMT_SCALAR, icx.FMT_SIMPLE8B):  # accepted, then refused for alignment
+        assert L.fastpfor_decode(a4, 64, a16, 128, icx.DELTA_1, fmt, None, a16, 1 << 20, None) == icx.EALIGN
+    # SIMD-BP128 calls accept BP32; a bad layout value is refused
+    assert L.bp128_decode(a4, 64, a16, 128, icx.DELTA_1, icx.FMT_BP32, None, a16, 1 << 20, None) == icx.EALIGN
+    assert L.bp128_decode(a16, 64, a16, 128, icx.DELTA_1, 9, None, a16, 1 << 20, None) == icx.EINVAL
+    # the fused consumer: BP32 refused, a count pointer required, alignment checked
+    b = (a16, 64, 128, icx.DELTA_1)
+    assert L.bp128_intersect(*b, icx.FMT_BP32, None, a16, 10, a16, a16, a16, 1 << 20, None) == icx.EINVAL
+    assert L.bp128_intersect(*b, icx.FMT_PAPER, None, a16, 10, a16, None, a16, 1 << 20, None) == icx.EINVAL
+    assert L.bp128_intersect(*b, icx.FMT_PAPER, None, vp(4098), 10, a16, a16, a16, 1 << 20, None) == icx.EALIGN
+    assert L.bp128_intersect(*b, icx.FMT_PAPER, None, a16, 10, a16, vp(4100), a16, 1 << 20, None) == icx.EALIGN
+    assert L.sorted_intersect(a16, 128, a16, 10, a16, None, None) == icx.EINVAL
+    assert L.sorted_intersect(a4, 128, a16, 10, a16, a16, None) == icx.EALIGN
+    # size helpers of the new layouts
+    assert icx.bp128_max_bytes(1 << 20, icx.FMT_BP32) >= (1 << 20) // 128 * 516
+    assert L.icx_fastpfor_max_bytes(1 << 20) >= (1 << 20) // 128 * (512 + 131 + 1024)
