@@ -31,15 +31,16 @@ def p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("fmt,delta", [(icx.FMT_PAPER, icx.DELTA_4), (icx.FMT_W32, icx.DELTA_1)])
+@pytest.mark.parametrize("fmt,delta", [(icx.FMT_PAPER, icx.DELTA_4), (icx.FMT_W32, icx.DELTA_1),
+                                       (icx.FMT_BP32, icx.DELTA_1)])
 def test_static_decode_matches_allocating_decode_twice(fmt, delta):
     fn = static_fn()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     inputs = [W.uniform_sorted(16384 * 9 + 2048 * 3 + 77, 29, 71), W.random_small(100_003, 72)]
     for x in inputs:  # two calls in a row, different streams of integers
-        enc = oracle.bp128_encode(x, delta, fmt)
+        enc = oracle.encode("bp128", x, delta, fmt)  # the BP32 layout goes to the BP32 coder
         d = torch.from_numpy(enc).cuda()
-        idx = torch.from_numpy(oracle.bp128_index(enc, x.size, fmt)).cuda()
+        idx = torch.from_numpy(oracle.index("bp128", enc, x.size, fmt)).cuda()
         want = icx.bp128_decode(d, x.size, delta, fmt, index=idx)
         out = torch.empty(x.size, dtype=torch.uint32, device="cuda")
         status = torch.full((1,), 99, dtype=torch.int32, device="cuda")
