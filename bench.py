@@ -220,6 +220,9 @@ def run_gpu(args, world, rank, local):
         icx.set_tuning("bp128.l2_prefetch", args.bp128_l2_prefetch)
     if args.fastpfor_warps:
         icx.set_tuning("fastpfor.warps_per_cta", args.fastpfor_warps)
+    for kv in args.tune:
+        key, _, val = kv.partition("=")
+        icx.set_tuning(key, int(val))
 
     arrays = workload_arrays(args.n)
     stream = torch.cuda.current_stream()
@@ -796,6 +799,8 @@ def main():
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
     ap.add_argument("--bp128-l2-prefetch", type=int, default=-1, help="1/0: L2 prefetch of the metablocks one grid ahead")
     ap.add_argument("--fastpfor-warps", type=int, default=0, help="warps per CTA of the SIMD-FastPFOR decoder")
+    ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                    help="library tuning key (icx_set_tuning), repeatable")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
     ap.add_argument("--skip-intersect", action="store_true", help="skip the decode-into-intersection leg")
     ap.add_argument("--skip-bp32", action="store_true", help="skip the scalar-layout (BP32, FastPFOR) decodes")

@@ -240,6 +240,22 @@ icx_status icx_set_tuning(const char* key, int value) {
         icx::set_fastpfor_warps(value);
         return ICX_OK;
     }
+    if (!strcmp(key, "bp128.blocklane")) {
+        icx::set_bp128_blocklane(value);
+        return ICX_OK;
+    }
+    if (!strcmp(key, "bp128.blocklane_store")) {
+        icx::set_bp128_blocklane_store(value);
+        return ICX_OK;
+    }
+    if (!strcmp(key, "bp128.blocklane_lead")) {
+        icx::set_bp128_blocklane_lead(value);
+        return ICX_OK;
+    }
+    if (!strcmp(key, "bp128.blocklane_ctas")) {
+        icx::set_bp128_blocklane_ctas(value);
+        return ICX_OK;
+    }
     if (!strcmp(key, "bp128.l2_prefetch")) {
         icx::set_bp128_prefetch(value);
         return ICX_OK;

@@ -314,8 +314,21 @@ static cudaError_t launch_bp128_w(const uint8_t* in, size_t in_bytes, uint32_t* 
     return launch_bp128<DELTA, FMT, 8>(in, in_bytes, out, n, index, h, s);
 }
 
+static bool g_bp128_blocklane = true;  // two-phase block-per-lane decoder for the paper layout with deltas
+
+void set_bp128_blocklane(int on) { g_bp128_blocklane = on != 0; }
+
 cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
                                 size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s) {
+    if (g_bp128_blocklane && fmt == ICX_FMT_PAPER && delta != ICX_DELTA_NONE)
+        return launch_bp128_blocklane(delta, in, in_bytes, out, n, index, h, s);
+    return launch_bp128_decode_lookback(delta, fmt, in, in_bytes, out, n, index, h, s);
+}
+
+// The single-pass decoder with a decoupled look-back; it uses only the
+// workspace header and look-back states.
+cudaError_t launch_bp128_decode_lookback(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
+                                         size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s) {
 #define ICX_CASE(D, F) \
     if (delta == D && fmt == F) return launch_bp128_w<D, F>(in, in_bytes, out, n, index, h, s);
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_PAPER)

@@ -52,10 +52,19 @@ __host__ __device__ inline size_t ws_unitmeta_off(size_t n) {
     return (end + 255) / 256 * 256;
 }
 // per unit of 16 blocks: page-relative offset and size of its packed low bits
-__host__ __device__ inline size_t ws_total_bytes(size_t n) {
+__host__ __device__ inline size_t ws_unitmeta_end(size_t n) {
     const size_t end = ws_unitmeta_off(n) + 8 * (n / 2048 + 2);
     return (end + 255) / 256 * 256;
 }
+// Two-phase SIMD-BP128 decoding: per 128-integer block four tagged 64-bit
+// words (block sums), per pair of metablocks two groups of four (pair total,
+// pair prefix), per group of 64 pairs one group of four (look-back state)
+// and a 32-bit counter.
+__host__ __device__ inline size_t ws_blocklane_bytes(size_t n) {
+    const size_t nb = n / 128, P = ((nb + 15) / 16 + 1) / 2, Gn = (P + 63) / 64;
+    return (32 * (nb + 1) + 64 * (P + 1) + 36 * (Gn + 1) + 255) / 256 * 256;
+}
+__host__ __device__ inline size_t ws_total_bytes(size_t n) { return ws_unitmeta_end(n) + ws_blocklane_bytes(n); }
 
 // A device wait that sees no progress for this long gives up with ETIMEOUT.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
@@ -125,6 +134,32 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // Hint: bring `bytes` (a multiple of 16) at the 16-byte aligned `src` into L2.
 __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// L2 eviction-priority policies for the cache-hinted copies below.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// bulk_load and prefetch_l2 with an L2 eviction policy for the source lines.
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_l2_hint(const void* src, uint32_t bytes, uint64_t policy) {
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes), "l"(policy)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -276,10 +311,10 @@ constexpr int kLookbackRows = 1;
 // published) from its predecessors' states and, if `publish`, publishes its
 // inclusive prefix.  Whole warp.
 template <int NL, int R = kLookbackRows>
-__device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg, bool publish = true) {
+__device__ uint4 lookback_resolve_at(unsigned long long* st, WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg,
+                                     bool publish = true) {
     static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
-    unsigned long long* st = tile_states(h);
     const uint32_t tagA = (epoch << 2) | 1u, tagP = (epoch << 2) | 2u;
     uint4 acc = make_uint4(0, 0, 0, 0);
     if (tile == 0) return acc;
@@ -353,6 +388,13 @@ __device__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, ui
         st_relaxed(st + (size_t)tile * kStatesPerTile + lane,
                    ((unsigned long long)tagP << 32) | (comp(acc, lane) + comp(agg, lane)));
     return acc;
+}
+
+// The same over the workspace's look-back states.
+template <int NL, int R = kLookbackRows>
+__device__ __forceinline__ uint4 lookback_resolve(WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg,
+                                                  bool publish = true) {
+    return lookback_resolve_at<NL, R>(tile_states(h), h, epoch, tile, agg, publish);
 }
 
 // Decoupled look-back of one tile: publish its aggregate, resolve its

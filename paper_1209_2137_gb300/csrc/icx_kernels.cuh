@@ -8,6 +8,10 @@ namespace icx {
 
 cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
                                 size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s);
+cudaError_t launch_bp128_decode_lookback(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
+                                         size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s);
+cudaError_t launch_bp128_blocklane(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                   const uint64_t* index, WsHeader* h, cudaStream_t s);
 cudaError_t launch_bp128_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
                                WsHeader* h, cudaStream_t s);
 cudaError_t launch_delta_decode(int delta, const uint32_t* in, uint32_t* out, size_t n, WsHeader* h,
@@ -31,6 +35,10 @@ cudaError_t launch_sorted_member(const uint32_t* a, size_t n, const uint32_t* b,
 size_t fastpfor_encode_workspace_bytes(size_t n);
 void set_bp128_warps(int w);
 void set_bp128_prefetch(int on);
+void set_bp128_blocklane(int on);
+void set_bp128_blocklane_store(int v);
+void set_bp128_blocklane_ctas(int v);
+void set_bp128_blocklane_lead(int v);
 void set_fastpfor_warps(int w);
 
 }  // namespace icx

@@ -69,7 +69,7 @@ extern "C" icx_status bp128_decode_static(const uint8_t* d_in, size_t in_bytes, 
         if (icx::launch_bp128_index(d_in, in_bytes, n, fmt, h->mini_index, h, s) != cudaSuccess) return ICX_ECUDA;
         d_index = h->mini_index;
     }
-    if (icx::launch_bp128_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s) != cudaSuccess)
+    if (icx::launch_bp128_decode_lookback(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s) != cudaSuccess)
         return ICX_ECUDA;
     if (d_status &&
         cudaMemcpyAsync(d_status, &h->status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
