@@ -248,6 +248,10 @@ icx_status icx_set_tuning(const char* key, int value) {
         icx::set_bp128_blocklane_store(value);
         return ICX_OK;
     }
+    if (!strcmp(key, "bp128.blocklane_sum_warps")) {
+        icx::set_bp128_blocklane_sumw(value);
+        return ICX_OK;
+    }
     if (!strcmp(key, "bp128.blocklane_lead")) {
         icx::set_bp128_blocklane_lead(value);
         return ICX_OK;

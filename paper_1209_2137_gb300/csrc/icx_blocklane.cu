@@ -104,6 +104,30 @@ __device__ __forceinline__ uint4 wait_tagged(const unsigned long long* p, uint32
     return v;
 }
 
+// NL tagged words loaded without looking at them yet, so the load is in
+// flight while the warp works; check_tagged reads them later.
+struct RawTagged {
+    unsigned long long w0, w1, w2, w3;
+};
+
+template <int NL>
+__device__ __forceinline__ void ld_raw(const unsigned long long* p, RawTagged& t) {
+    if (NL == 1) {
+        t.w0 = ld_relaxed(p);
+        t.w1 = t.w2 = t.w3 = 0;
+    } else {
+        ld_relaxed_v2(p, t.w0, t.w1);
+        ld_relaxed_v2(p + 2, t.w2, t.w3);
+    }
+}
+
+template <int NL>
+__device__ __forceinline__ bool check_tagged(const RawTagged& t, uint32_t tag, uint4& v) {
+    v = make_uint4((uint32_t)t.w0, (uint32_t)t.w1, (uint32_t)t.w2, (uint32_t)t.w3);
+    return (uint32_t)(t.w0 >> 32) == tag &&
+           (NL == 1 || ((uint32_t)(t.w1 >> 32) == tag && (uint32_t)(t.w2 >> 32) == tag && (uint32_t)(t.w3 >> 32) == tag));
+}
+
 // Output store paths of pass 2.
 constexpr int kStoreRestage = 0;  // 8 fields of every block through shared memory, then coalesced 16-byte stores
 constexpr int kStoreV8 = 1;       // each lane stores its own 32-byte field pairs (output 32-byte aligned)
@@ -210,10 +234,10 @@ __device__ __forceinline__ void emit_field(Walk& w, uint4 f, int r, int i) {
         w.acc = add4(w.acc, f);
         o = w.acc;
     } else {
-        o.x = w.acc.x + f.x;
-        o.y = o.x + f.y;
-        o.z = o.y + f.z;
-        o.w = o.z + f.w;
+        // the prefixes inside the field do not wait for the running sum, so
+        // the sum's chain is one add per field
+        const uint32_t p1 = f.x + f.y, p2 = p1 + f.z, p3 = p2 + f.w;
+        o = make_uint4(w.acc.x + f.x, w.acc.x + p1, w.acc.x + p2, w.acc.x + p3);
         w.acc.x = o.w;
     }
     if constexpr (STORE == kStoreRestage) {
@@ -235,8 +259,8 @@ __device__ __forceinline__ void emit_field(Walk& w, uint4 f, int r, int i) {
 // width of the pair at most 32 / FPS, the FPS fields from the current bit
 // offset all lie in one 32-bit funnel shift of the window, so the window
 // moves once per FPS fields.
-template <int DELTA, bool DECODE, int STORE, int FPS, class Rows>
-__device__ __forceinline__ void walk_block(const Rows& rows, Walk& w) {
+template <int DELTA, bool DECODE, int STORE, int FPS, class Rows, class Mid>
+__device__ __forceinline__ void walk_block(const Rows& rows, Walk& w, Mid& mid) {
     const uint32_t b2 = 2 * w.b, b3 = 3 * w.b, step = FPS * w.b;
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
@@ -271,6 +295,7 @@ __device__ __forceinline__ void walk_block(const Rows& rows, Walk& w) {
             }
             __syncwarp();
         }
+        if (c == 0) mid();
     }
 }
 
@@ -278,10 +303,11 @@ __device__ __forceinline__ void walk_block(const Rows& rows, Walk& w) {
 // false) returns the block's sum (stride 4: one per residue, stride 1: in
 // .x).  Pass B decodes the block with `carry` (its exclusive prefix) and
 // writes it.  A metablock whose widths exceed 32 or disagree with its size is
-// recorded as corrupt and decoded as zeros.
-template <int DELTA, bool DECODE, int STORE, class Rows>
+// recorded as corrupt and decoded as zeros.  `mid` runs once, after the
+// first quarter of the fields (the caller's work that should overlap them).
+template <int DELTA, bool DECODE, int STORE, class Rows, class Mid>
 __device__ __forceinline__ uint4 pair_blocks(const Rows& rows, const Pair& d, uint4 carry, uint32_t* __restrict__ out,
-                                             size_t pair_first, uint8_t* rest, WsHeader* h, int lane) {
+                                             size_t pair_first, uint8_t* rest, WsHeader* h, int lane, Mid& mid) {
     const int m = lane >> 4, k = lane & 15;
     const uint32_t K = m ? d.K1 : d.K0;
     const bool in_meta = (uint32_t)m < d.mcount;
@@ -330,11 +356,11 @@ __device__ __forceinline__ uint4 pair_blocks(const Rows& rows, const Pair& d, ui
     // fields per window step, the same for the whole warp
     const uint32_t maxb = __reduce_max_sync(FULL, b);
     if (maxb <= 8)
-        walk_block<DELTA, DECODE, STORE, 4>(rows, w);
+        walk_block<DELTA, DECODE, STORE, 4>(rows, w, mid);
     else if (maxb <= 16)
-        walk_block<DELTA, DECODE, STORE, 2>(rows, w);
+        walk_block<DELTA, DECODE, STORE, 2>(rows, w, mid);
     else
-        walk_block<DELTA, DECODE, STORE, 1>(rows, w);
+        walk_block<DELTA, DECODE, STORE, 1>(rows, w, mid);
     if constexpr (DECODE) {
         return make_uint4(0, 0, 0, 0);
     } else {
@@ -383,7 +409,7 @@ template <int DELTA, int STORE>
 __global__ void __maxnreg__(96)
     bp128_blocklane_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
                            const uint64_t* __restrict__ index, WsHeader* h, bl::Scratch sc, uint32_t tail,
-                           uint32_t lead) {
+                           uint32_t lead, uint32_t sumw) {
     using namespace bl;
     constexpr int NL = DELTA == ICX_DELTA_4 ? 4 : 1;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -410,14 +436,22 @@ __global__ void __maxnreg__(96)
     // Task ids come from one counter; the atomic for a task is issued an
     // iteration before its value is used (take_async, then task_of).
     // Task kinds: 0 = A (sum), 1 = B (decode), 2 = tail, 3 = none left.
+    // With sumw > 0 the first sumw warps of every CTA take only A tasks (pairs
+    // in order, from the tile counter) and the others only B tasks (pairs in
+    // order, then the tail, from aux[0]).
+    const int role = sumw == 0 ? 0 : (warp < (int)sumw ? 1 : 2);
+    unsigned int* const ctr = role == 2 ? &h->aux[0] : &h->tile_counter;
     auto take_async = [&]() -> uint32_t {
         uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(&h->tile_counter, 1u);
+        if (lane == 0) u = atomicAdd(ctr, 1u);
         return u;
     };
     auto task_of = [&](uint32_t raw, uint32_t& kind, uint32_t& p) {
         const uint32_t u = __shfl_sync(FULL, raw, 0);
-        if (u >= ntasks) {
+        if (role != 0) {
+            p = u;
+            kind = role == 1 ? (u < P ? 0u : 3u) : (u < P ? 1u : (u == P && tail) ? 2u : 3u);
+        } else if (u >= ntasks) {
             kind = 3;
             p = 0;
         } else if (u < L0) {
@@ -440,8 +474,11 @@ __global__ void __maxnreg__(96)
             p = b;
         }
     };
-    auto pair_at = [&](uint32_t p) -> Pair {
-        const uint64_t e = lane < 3 ? __ldg(index + min((size_t)2 * p + lane, M)) : 0ull;
+    // the index entries of pair p (lanes 0..2), then the pair they describe
+    auto index_entry = [&](uint32_t p) -> uint64_t {
+        return lane < 3 ? __ldg(index + min((size_t)2 * p + lane, M)) : 0ull;
+    };
+    auto pair_from = [&](uint32_t p, uint64_t e) -> Pair {
         const uint64_t a = __shfl_sync(FULL, e, 0), b1 = __shfl_sync(FULL, e, 1), c = __shfl_sync(FULL, e, 2);
         Pair d;
         const size_t mb = 2 * (size_t)p;
@@ -514,42 +551,56 @@ __global__ void __maxnreg__(96)
         if (p0 < P) st_tagged<NL>(sc.pre + 4 * (size_t)p0, tagI, e0);
         if (p0 + 1 < P) st_tagged<NL>(sc.pre + 4 * (size_t)(p0 + 1), tagI, add4(e0, v0));
     };
-    // prefix and block sums of a B task, loaded one task ahead (and waited
-    // for only if they were not yet published)
-    auto load_b = [&](uint32_t p, uint4& pv, bool& pok, uint4& bv, bool& bok) {
-        pok = ld_tagged<NL>(sc.pre + 4 * (size_t)p, tagI, pv);
+    // prefix and block sums of a B task: loaded one task ahead, looked at
+    // when the task starts (and waited for only if they were not yet
+    // published)
+    RawTagged pr, br;
+    auto load_b = [&](uint32_t p) {
+        ld_raw<NL>(sc.pre + 4 * (size_t)p, pr);
         const size_t blk = 32 * (size_t)p + lane;
-        bok = true;
-        bv = make_uint4(0, 0, 0, 0);
-        if (blk < nb) bok = ld_tagged<NL>(sc.bst + 4 * blk, tagA, bv);
+        if (blk < nb) ld_raw<NL>(sc.bst + 4 * blk, br);
     };
 
     uint32_t kc, pc, kn, pn;
     task_of(take_async(), kc, pc);
     Pair dc;
     uint32_t s_cur = 0;
-    uint4 pre_c = make_uint4(0, 0, 0, 0), bs_c = pre_c;
-    bool pre_ok = false, bs_ok = false;
     if (kc <= 1) {
-        dc = pair_at(pc);
+        dc = pair_from(pc, index_entry(pc));
         s_cur = issue(dc, kc == 0 ? keep : drop);
-        if (kc == 1) load_b(pc, pre_c, pre_ok, bs_c, bs_ok);
+        if (kc == 1) load_b(pc);
     }
     task_of(take_async(), kn, pn);
+    uint64_t en = kn <= 1 ? index_entry(pn) : 0ull;
     while (kc != 3) {
-        const uint32_t raw2 = take_async();  // the task after next
+        // the current B task's prefix and block sum, loaded an iteration ago
+        uint4 pre_c = make_uint4(0, 0, 0, 0), bs_c = pre_c;
+        bool pre_ok = true, bs_ok = true;
+        if (kc == 1) {
+            pre_ok = check_tagged<NL>(pr, tagI, pre_c);
+            if (32 * (size_t)pc + lane < nb) bs_ok = check_tagged<NL>(br, tagA, bs_c);
+        }
+        // the task after next: its id is taken now and read, with its index
+        // entries requested, a quarter of the way through the current task
+        const uint32_t raw2 = take_async();
+        uint32_t kk = 3, pk = 0;
+        uint64_t ek = 0;
+        bool mid_done = false;
+        auto mid = [&]() {
+            task_of(raw2, kk, pk);
+            ek = kk <= 1 ? index_entry(pk) : 0ull;
+            mid_done = true;
+        };
         Pair dn;
         uint32_t s_nx = 0;
         bool nx_issued = false;
-        uint4 pre_n = make_uint4(0, 0, 0, 0), bs_n = pre_n;
-        bool pre_nok = false, bs_nok = false;
         if (kn <= 1) {
-            dn = pair_at(pn);
+            dn = pair_from(pn, en);
             if (kc > 1 || fits(dc, dn)) {
                 s_nx = issue(dn, kn == 0 ? keep : drop);
                 nx_issued = true;
             }
-            if (kn == 1) load_b(pn, pre_n, pre_nok, bs_n, bs_nok);
+            if (kn == 1) load_b(pn);
         }
         if (kc == 0) {
             // ------------------------------------------------------ A task
@@ -569,10 +620,10 @@ __global__ void __maxnreg__(96)
                 } else if (space(dc)) {
                     bs = pair_blocks<DELTA, false, 0>(
                         SmemRows{ring + slot(s_cur, dc), smem_u32(ring + slot(s_cur, dc))}, dc, bs, out, 0, rest, h,
-                        lane);
+                        lane, mid);
                 } else {
                     bs = pair_blocks<DELTA, false, 0>(GlobalRows{in + dc.start, in_bytes - dc.start}, dc, bs, out, 0,
-                                                      rest, h, lane);
+                                                      rest, h, lane, mid);
                 }
             }
             __syncwarp();
@@ -599,10 +650,10 @@ __global__ void __maxnreg__(96)
                 const size_t first = 4096 * (size_t)pc;
                 if (space(dc))
                     pair_blocks<DELTA, true, STORE>(SmemRows{ring + slot(s_cur, dc), smem_u32(ring + slot(s_cur, dc))},
-                                                    dc, carry, out, first, rest, h, lane);
+                                                    dc, carry, out, first, rest, h, lane, mid);
                 else
                     pair_blocks<DELTA, true, STORE>(GlobalRows{in + dc.start, in_bytes - dc.start}, dc, carry, out,
-                                                    first, rest, h, lane);
+                                                    first, rest, h, lane, mid);
             }
             __syncwarp();
         } else {
@@ -634,16 +685,15 @@ __global__ void __maxnreg__(96)
                 if (q0 + c < n) out[q0 + c] = comp(o, c);
             __syncwarp();
         }
+        if (!mid_done) mid();  // the task had no fields to walk
         if (kn <= 1 && !nx_issued) s_nx = issue(dn, kn == 0 ? keep : drop);
         kc = kn;
         pc = pn;
-        task_of(raw2, kn, pn);
+        kn = kk;
+        pn = pk;
+        en = ek;
         dc = dn;
         s_cur = s_nx;
-        pre_c = pre_n;
-        pre_ok = pre_nok;
-        bs_c = bs_n;
-        bs_ok = bs_nok;
     }
     // a copy that never landed must not outlive the CTA's shared memory
     if (broken)
@@ -661,6 +711,7 @@ __global__ void __maxnreg__(96)
         for (uint32_t i = threadIdx.x; i < Gn; i += blockDim.x) sc.gcnt[i] = 0;
         if (threadIdx.x == 0) {
             h->tile_counter = 0;
+            h->aux[0] = 0;
             h->done_counter = 0;
             atomicExch(&h->epoch, (epoch + 1u) & 0x3FFFFFFFu);
         }
@@ -686,6 +737,12 @@ void set_bp128_blocklane_ctas(int v) { g_blocklane_ctas = v > 0 ? v : 0; }
 static int g_blocklane_lead = 0;
 
 void set_bp128_blocklane_lead(int v) { g_blocklane_lead = v > 0 ? v : 0; }
+
+// Warps per CTA that only sum (the others only decode); 0: every warp takes
+// both kinds of task from one counter.
+static int g_blocklane_sumw = 0;
+
+void set_bp128_blocklane_sumw(int v) { g_blocklane_sumw = (v > 0 && v < bl::kW) ? v : 0; }
 
 // Scratch layout of a decode of n integers inside workspace h.
 static bl::Scratch blocklane_scratch(WsHeader* h, size_t n) {
@@ -724,7 +781,8 @@ static cudaError_t launch_blocklane_t(const uint8_t* in, size_t in_bytes, uint32
     if (g_blocklane_ctas > 0 && (size_t)g_blocklane_ctas < G) G = (size_t)g_blocklane_ctas;
     const size_t lead = max((size_t)128, g_blocklane_lead > 0 ? (size_t)g_blocklane_lead : 2 * G * bl::kW);
     kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, h, blocklane_scratch(h, n),
-                                            (uint32_t)(n - 128 * nb), (uint32_t)min(lead, (size_t)0xFFFFFFFFu));
+                                            (uint32_t)(n - 128 * nb), (uint32_t)min(lead, (size_t)0xFFFFFFFFu),
+                                            (uint32_t)g_blocklane_sumw);
     return cudaGetLastError();
 }
 

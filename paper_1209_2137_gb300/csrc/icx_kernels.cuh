@@ -39,6 +39,7 @@ void set_bp128_blocklane(int on);
 void set_bp128_blocklane_store(int v);
 void set_bp128_blocklane_ctas(int v);
 void set_bp128_blocklane_lead(int v);
+void set_bp128_blocklane_sumw(int v);
 void set_fastpfor_warps(int w);
 
 }  // namespace icx

@@ -82,11 +82,21 @@ def test_blocklane_variants_match_oracle(streams):
                 if codec == "bp128" and fmt == icx.FMT_PAPER:
                     assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("lead", lead, delta)
         icx.set_tuning("bp128.blocklane_lead", 0)
+        for sumw in (1, 2, 5):  # warps specialised for summing and decoding
+            icx.set_tuning("bp128.blocklane_sum_warps", sumw)
+            for ctas in (0, 1):
+                icx.set_tuning("bp128.blocklane_ctas", ctas)
+                for codec, delta, fmt, enc, idx, want in streams:
+                    if codec == "bp128" and fmt == icx.FMT_PAPER:
+                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("sum warps", sumw, ctas)
+        icx.set_tuning("bp128.blocklane_sum_warps", 0)
+        icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane", 0)
         for codec, delta, fmt, enc, idx, want in streams:
             if codec == "bp128" and fmt == icx.FMT_PAPER:
                 assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("single pass", delta)
     finally:
+        icx.set_tuning("bp128.blocklane_sum_warps", 0)
         icx.set_tuning("bp128.blocklane", 1)
         icx.set_tuning("bp128.blocklane_store", -1)
         icx.set_tuning("bp128.blocklane_ctas", 0)
