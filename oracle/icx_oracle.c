@@ -5,7 +5,7 @@
  * that each routine can be checked against the paper's definitions by eye.
  * Section / figure references are to Lemire & Boytsov, arXiv 1209.2137.
  *
- * Readings of points the paper leaves open (same list as the design notes):
+ * Readings of points the paper leaves open:
  *  R1  n/128 full blocks are grouped 16 per metablock (the last may hold
  *      fewer, its descriptor stays 16 bytes with unused width bytes 0); the
  *      remaining n % 128 integers are Variable-Byte coded after the last
@@ -34,6 +34,21 @@
  *      j at byte 128*w + 4*j).  Lane j = 4*g + l holds, for every block k in
  *      order, the four integers 128*k + 16*g + 4*m + l (m = 0..3) at width
  *      b_k; the lane is ceil(4*sum(b_k)/32) words long.
+ *  R17 a FastPFOR record with more than 128 exceptions is corrupt (a block
+ *      holds 128 values).
+ *  R18 the width choice costs an exception 8 + (maxbits - b) bits, with the
+ *      block length (128) in place of the worked example's 16.
+ *  R19 the decode fused into a consumer computes membership of a sorted
+ *      query list in the decoded sorted list (bit j set iff b[j] occurs).
+ *  R20 BP32: per 128 integers a little-endian descriptor word (byte j = width
+ *      of 32-integer block j) and four one-lane blocks; the remainder in
+ *      Variable Byte (as R1).
+ *  R21 the scalar FastPFOR: the same pages with one-lane packing, exception
+ *      arrays padded to 32 values, sections still 16-byte aligned.
+ *  R22 SimplePFOR: the scalar page with one Simple-8b stream of the page's
+ *      exception high parts (selector in bits 60..63) instead of the arrays.
+ *  R23 the Simple-8b encoder takes a selector only when all of its count of
+ *      next integers exist (no partial final word).
  */
 #include "icx_oracle.h"
 

@@ -9,8 +9,8 @@
  *
  * Every routine is a literal, bit-by-bit restatement of the definitions in
  * the paper (section numbers given beside each entry point).  Where the paper
- * is silent, the reading used is named R1..R16; the same list is kept in the
- * design notes of the repository.
+ * is silent, the reading used is named R1..R23; all are stated at the top
+ * of icx_oracle.c.
  *
  * All integers are uint32; all delta arithmetic is modulo 2^32.
  * Return codes: 0 = ok, 3 = corrupt stream (same numbering as the library).

@@ -1,10 +1,11 @@
 """A second, independent reader of the stream layouts, used by the tests.
 
-It walks the byte layout with Python integers (structure only: widths,
-records, counts and sizes) so that the oracle's encoder can be checked
-against the format definitions without trusting the oracle's own parser.
-Layouts: SIMD-BP128 metablocks (Sec. 6.2), the W32 variant, SIMD-FastPFOR
-pages (Sec. 5); readings R1-R16 are listed in the oracle's header.
+It walks the byte layout with Python integers -- the structure (widths,
+records, counts and sizes) and the coded values themselves -- so that the
+oracle's encoder can be checked against the format definitions without
+trusting the oracle's own parser.  Layouts: SIMD-BP128 metablocks (Sec. 6.2)
+and the W32 variant, SIMD-FastPFOR pages (Sec. 5), BP32, the scalar FastPFOR
+and SimplePFOR; readings R1-R23 are listed in the oracle's header.
 """
 from __future__ import annotations
 
@@ -181,3 +182,109 @@ def simplepfor_read(buf, n, table):
         pages.append(dict(offset=base, N=N, W=W, words=words, sels=sels, high=high, size=end - base))
         pos = end
     return pages, out, pos
+
+
+# -- values of the SIMD layouts, rebuilt from the bytes --------------------
+
+def lane_bits(buf, off, words, lanes, lane):
+    """The bit string of one lane of an interleaved block: word w of the lane
+    sits at byte off + 4 * (lanes * w + lane), little endian; word w holds
+    bits [32w, 32w + 32) of the lane's string."""
+    out = 0
+    for w in range(words):
+        out |= le32(buf, off + 4 * (lanes * w + lane)) << (32 * w)
+    return out
+
+
+def vertical_values(buf, off, b, count=128):
+    """Values 0..count-1 of a 4-lane vertical block of width b at `off`
+    (Sec. 4, Figs. 6-7): value i is field i // 4 of lane i % 4."""
+    if b == 0:
+        return [0] * count
+    words = (count // 4 * b + 31) // 32
+    lanes = [lane_bits(buf, off, words, 4, l) for l in range(4)]
+    mask = (1 << b) - 1
+    return [(lanes[i % 4] >> ((i // 4) * b)) & mask for i in range(count)]
+
+
+def vbyte_read(buf, pos, count):
+    """Variable Byte (Sec. 2.4): 7 data bits per byte, low group first, high
+    bit set on the last byte of each integer."""
+    out = []
+    for _ in range(count):
+        v, shift = 0, 0
+        while True:
+            byte = buf[pos]
+            pos += 1
+            v |= (byte & 0x7F) << shift
+            shift += 7
+            if byte & 0x80:
+                break
+        out.append(v)
+    return out, pos
+
+
+def bp128_read(buf, n, layout):
+    """SIMD-BP128 (layout 0, Sec. 6.2) or W32 (layout 1, R16): every coded
+    delta of the stream, the n // 128 full blocks from the packed bits and the
+    n % 128 last ones from the Variable Byte tail."""
+    buf = bytes(memoryview(buf))
+    metas, tail = bp128_walk(buf, n, layout)
+    out = []
+    for off, widths, size, k in metas:
+        if layout == 0:
+            q = off + 16
+            for b in widths[:k]:
+                out.extend(vertical_values(buf, q, b))
+                q += 16 * b
+        else:
+            # lane j = 4g + l: block after block, the integers 16g + 4m + l
+            # (m = 0..3) at width b_k, fields packed on from the previous block
+            words = (size - 16) // 128
+            lanes = [lane_bits(buf, off + 16, words, 32, j) for j in range(32)]
+            bit = 0
+            for b in widths[:k]:
+                blk = [0] * 128
+                mask = (1 << b) - 1
+                for j in range(32):
+                    g, l = divmod(j, 4)
+                    for m in range(4):
+                        blk[16 * g + 4 * m + l] = (lanes[j] >> (bit + m * b)) & mask
+                out.extend(blk)
+                bit += 4 * b
+    rest, end = vbyte_read(buf, tail, n - 128 * (n // 128))
+    return out + rest, end
+
+
+def fastpfor_simd_read(buf, n):
+    """SIMD-FastPFOR (Sec. 5, SIMD variant): every full block's coded values
+    from the page bytes: the low parts in the vertical layout, the exception
+    arrays as vertical blocks of 128 values (element q of array d is value
+    q % 128 of the chunk q // 128, each chunk 16 * d bytes), OR-ed in at their
+    positions in block order; the Variable Byte tail after the last page."""
+    buf = bytes(memoryview(buf))
+    pages, tail = fastpfor_walk(buf, n, chunk=128)
+    out = []
+    for pg in pages:
+        base = pg["offset"]
+        arrays = {}
+        for d, (cnt, off) in pg["arrays"].items():
+            vals = []
+            for c in range((cnt + 127) // 128):
+                vals.extend(vertical_values(buf, off + 16 * d * c, d))
+            arrays[d] = vals[:cnt]
+        cursor = {d: 0 for d in arrays}
+        packed = base + 16
+        for b, mb, pos_list in pg["records"]:
+            vals = vertical_values(buf, packed, b)
+            packed += 16 * b
+            if mb > b:
+                d = mb - b
+                for p in pos_list:
+                    vals[p] |= arrays[d][cursor[d]] << b
+                    cursor[d] += 1
+            out.extend(vals)
+        for d in arrays:
+            assert cursor[d] == len(arrays[d]), (d, cursor[d], len(arrays[d]))
+    rest, end = vbyte_read(buf, tail, n - 128 * (n // 128))
+    return pages, out + rest, end

@@ -393,6 +393,56 @@ def test_fastpfor_every_exception_width_and_count():
             pages, _ = F.fastpfor_walk(enc, x.size)
             assert pages[0]["arrays"][d][0] == total
             assert np.array_equal(oracle.fastpfor_decode(enc, x.size, 0), x)
+            # the values read back independently: array d in chunks of 128
+            # vertically packed values (element q: chunk q // 128, lane q % 4,
+            # field (q % 128) // 4)
+            _, vals, end = F.fastpfor_simd_read(enc, x.size)
+            assert vals == [int(v) for v in x] and end == enc.size, (d, total)
+
+
+def _diffs(x, delta):
+    # closed-form differences (Sec. 3): x_i - x_{i-s} mod 2^32, x_i for i < s
+    s = delta if delta else 1
+    xi = [int(v) for v in x]
+    return [(xi[i] - (xi[i - s] if (delta and i >= s) else 0)) % (1 << 32) for i in range(len(xi))]
+
+
+@pytest.mark.parametrize("layout", [oracle.PAPER, oracle.W32])
+def test_bp128_values_read_back_independently(layout):
+    # Sec. 4 (Figs. 6-7) and Sec. 6.2: every coded delta, rebuilt from the
+    # bytes with Python integers (word w of lane l at byte 16w + 4l, value i
+    # = field i // 4 of lane i % 4; W32 per R16), equals the closed-form
+    # difference of the input, for strides 0, 1 and 4, partial metablocks
+    # and Variable Byte tails; random widths 0..32 cover every field width
+    cases = [(n, W.uniform_sorted(n, 26, 700 + n % 91)) for n in
+             (1, 127, 128, 129, 2047, 2048, 2049, 4096 + 77, 16 * 128 * 3 + 5, 65536 + 130)]
+    cases.append((16 * 128 * 2 + 40, W.random_small(16 * 128 * 2 + 40, 77)))
+    for n, x in cases:
+        for delta in (0, 1, 4):
+            if delta and np.any(x[1:] < x[:-1]):
+                continue
+            enc = oracle.bp128_encode(x, delta, layout)
+            vals, end = F.bp128_read(enc, n, layout)
+            assert vals == _diffs(x, delta), (n, delta, layout)
+            assert end == enc.size
+
+
+def test_fastpfor_simd_values_read_back_independently():
+    # Sec. 5 (SIMD variant): every coded value of multi-page streams (the
+    # vertical low parts, the exception arrays in vertical chunks of 128, the
+    # positions) rebuilt from the bytes equals the closed-form difference of
+    # the input, for strides 0, 1 and 4
+    cases = [W.uniform_sorted(65536 * 2 + 128 * 7 + 99, 27, 61), W.exception_heavy(65536 + 128 * 3 + 5, 62),
+             W.random_small(65536 + 2048 + 17, 63)]
+    for x in cases:
+        for delta in (0, 1, 4):
+            if delta and np.any(x[1:] < x[:-1]):
+                continue
+            enc = oracle.fastpfor_encode(x, delta)
+            pages, vals, end = F.fastpfor_simd_read(enc, x.size)
+            assert vals == _diffs(x, delta), delta
+            assert end == enc.size
+            assert len(pages) == (x.size // 128 + 511) // 512
 
 
 def test_fastpfor_lengths_and_pages():
