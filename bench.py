@@ -43,9 +43,9 @@ COMBOS = [
     ("fastpfor", 1, 0, "SIMD-FastPFOR"),
     ("fastpfor", 4, 0, "SIMD-FastPFOR*"),
 ]
-def kernel_name(codec: str, delta: int) -> str:
+def kernel_name(codec: str, delta: int, fmt: int = 0) -> str:
     if codec == "bp128":
-        return "bp128_decode_kernel"
+        return "bp128_blocklane_kernel" if fmt == 0 and delta else "bp128_decode_kernel"
     return "fastpfor_decode_pipe_kernel" if delta == 4 else "fastpfor_decode_kernel"
 
 
@@ -316,7 +316,7 @@ def run_gpu(args, world, rank, local):
     traffic = None if args.n else recorded_traffic(f"{ds['array']}:{ds['label']}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"{kernel_name(ds['codec'], ds['delta'])} ({ds['label']}, {ds['array']})",
+                "kernel": f"{kernel_name(ds['codec'], ds['delta'], ds['fmt'])} ({ds['label']}, {ds['array']})",
                 "alg_bytes_per_launch": ds["alg_bytes"], "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"}
     headline = next(i for i, s in enumerate(streams) if s["label"] == "SIMD-BP128*" and s["array"] == "uniform")
 

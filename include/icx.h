@@ -120,7 +120,9 @@ size_t icx_encode_workspace_bytes(size_t n);
 
 /* Zero a workspace before its first use (asynchronous on `stream`).  A
  * workspace resets itself at the end of every launch; one workspace must not
- * be used by two launches that can run at the same time. */
+ * be used by two launches that can run at the same time.  Its look-back
+ * states are tagged with a 30-bit launch number: a workspace that serves
+ * more than 2^30 launches must be zeroed again before then. */
 icx_status icx_workspace_init(void *d_workspace, size_t workspace_bytes, icx_stream_t stream);
 
 /* Synchronises `stream`, copies the workspace's status word to *out and
@@ -218,11 +220,17 @@ icx_status sorted_intersect(const uint32_t *d_a, size_t n, const uint32_t *d_b, 
  * reaches it.  No allocation happens in this call, and it calls no
  * allocating library routine.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array: two calls that
- * overlap on the GPU (other streams, other host threads) race and give wrong
- * results; serialise them. */
+ * Every call made outside stream capture looks up the array's device
+ * address (cudaGetSymbolAddress, with the current device), so the call stays
+ * valid after a device reset reloads the library's module; a call made while
+ * `stream` is being captured uses the address of the last uncaptured call on
+ * that device, so make one call on the device before any capture (ICX_EINVAL
+ * otherwise), and no device reset between that call and the capture.  All
+ * calls share the one array: two calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results; serialise them.
+ * Its look-back states are tagged with a 30-bit launch number; the call
+ * zeroes the array again (an asynchronous memset on `stream`) every 2^29
+ * calls on a device, before a tag could repeat. */
 icx_status bp128_decode_static(const uint8_t *d_in, size_t in_bytes, uint32_t *d_out, size_t n,
                                icx_delta delta, icx_layout fmt, const uint64_t *d_index,
                                uint32_t *d_status, icx_stream_t stream);

@@ -101,7 +101,7 @@ icx_status bp128_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out, s
         if (st != ICX_OK) return st;
         d_index = h->mini_index;
     }
-    return from_cuda(icx::launch_bp128_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s));
+    return from_cuda(icx::launch_bp128_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, ws_bytes, s));
 }
 
 // Clears the bitmap and the count of a membership call.

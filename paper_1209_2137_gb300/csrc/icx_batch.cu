@@ -975,7 +975,8 @@ icx_status icx_plan_launch_per_list(icx_plan* p, icx_stream_t stream) {
             if (!l.n) continue;
             const uint64_t* index = p->host_lists[i].index;
             if (l.codec == ICX_CODEC_BP128)
-                le = launch_bp128_decode(l.delta, l.fmt, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
+                le = launch_bp128_decode(l.delta, l.fmt, l.d_in, l.in_bytes, l.d_out, l.n, index, h,
+                                         p->single_ws_bytes, p->cap);
             else
                 le = launch_fastpfor_decode(l.delta, ICX_FMT_PAPER, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
         }

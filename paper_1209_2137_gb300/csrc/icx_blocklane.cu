@@ -12,16 +12,16 @@
 // Carries come from summing the blocks first instead of a chained
 // look-back.  An A task sums the blocks of one metablock pair and publishes
 // the block sums and the pair total; the A task that completes a group of
-// 64 pairs adds the group up, runs a decoupled look-back over the groups
-// and publishes every pair's exclusive prefix.  A B task copies the same pair
+// 64 pairs adds the group up, runs a decoupled look-back over the groups and
+// publishes every pair's exclusive prefix.  A B task copies the same pair
 // again (from L2), gives every lane its block's carry (pair prefix plus the
 // block sums before it in the pair) and decodes and writes each integer
-// once.  Warps take tasks from one counter: A tasks alone for a lead of
-// pairs, then A and B tasks alternately (A runs a lead ahead of B), then the
-// remaining B tasks, so the summing (compute bound) overlaps the stores
-// (bandwidth bound).  Every task waits only for tasks taken before it, and
-// every published value is a set of 64-bit words tagged with the launch
-// epoch, so readers need no fences.
+// once.  Warps take tasks from one counter: A tasks alone
+// for a lead of pairs, then A and B tasks alternately (A runs a lead ahead of
+// B), then the remaining B tasks, so the summing (compute bound) overlaps the
+// stores (bandwidth bound).  Every task waits only for tasks taken before
+// it, and every published value is a set of 64-bit words tagged with the
+// launch epoch, so readers need no fences.
 #include <cstddef>
 
 #include "icx_bp128.cuh"
@@ -46,17 +46,19 @@ struct Hdr {
 };
 static_assert(sizeof(Hdr) <= kHdr, "header");
 
-// Workspace region of the decoder (after the regions the other decoders
-// use): tagged block sums (four 64-bit words per block), pair totals and pair
-// prefixes (four words per pair each), group look-back states (four words
-// per group) and a counter per group.  A word holds (epoch << 2 | flag) in
-// its high half.
+// Workspace region of the decoder, at the end of the caller's workspace
+// (above every region the other decoders write for any length the workspace
+// is sized for): tagged block sums (four 64-bit words per block), pair totals
+// and pair prefixes (four words per pair each), group look-back states (four
+// words per group), and a counter per group.  A word holds
+// (epoch << 2 | flag) in its high half, so nothing tagged needs clearing; the
+// counters are zeroed at the start of every launch by the first CTA to run.
 struct Scratch {
     unsigned long long* bst;
     unsigned long long* ptot;
     unsigned long long* pre;
     unsigned long long* gst;
-    unsigned int* gcnt;  // pairs of each group summed so far (zeroed by the last CTA)
+    unsigned int* gcnt;
 };
 
 // NL tagged words (one per chain) written by one thread.
@@ -431,7 +433,16 @@ __global__ void __maxnreg__(96)
         mbar_init(bar + 1, 1);
     }
     fence_mbar_init();
-    __syncwarp();
+    // the first CTA to start zeroes the group counters, then raises aux[3]
+    if (threadIdx.x == 0) S.last = atomicAdd(&h->aux[4], 1u) == 0 ? 1u : 0u;
+    __syncthreads();
+    if (S.last) {
+        for (uint32_t i = threadIdx.x; i < Gn; i += blockDim.x) sc.gcnt[i] = 0;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&h->aux[3], epoch + 1u);
+    }
+    bool counters_ready = false;
 
     // Task ids come from one counter; the atomic for a task is issued an
     // iteration before its value is used (take_async, then task_of).
@@ -633,6 +644,22 @@ __global__ void __maxnreg__(96)
             const size_t blk = 32 * (size_t)pc + lane;
             if (blk < nb) st_tagged<NL>(sc.bst + 4 * blk, tagA, bs);
             const uint4 tot = warp_sum<NL>(bs);
+            // the group's counter (zeroed by the first CTA of this launch,
+            // which raises aux[3] to epoch + 1 when done)
+            if (!counters_ready) {
+                if (lane == 0) {
+                    const unsigned long long t0 = globaltimer();
+                    while (ld_acquire_u32(&h->aux[3]) != epoch + 1u) {
+                        if (globaltimer() - t0 > kWaitLimitNs) {
+                            set_error(h, ICX_ETIMEOUT);
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                __syncwarp();
+                counters_ready = true;
+            }
             const uint32_t g = pc / kGroup;
             uint32_t last = 0;
             if (lane == 0) {
@@ -708,10 +735,10 @@ __global__ void __maxnreg__(96)
     __syncthreads();
     if (S.last) {
         __threadfence();
-        for (uint32_t i = threadIdx.x; i < Gn; i += blockDim.x) sc.gcnt[i] = 0;
         if (threadIdx.x == 0) {
             h->tile_counter = 0;
             h->aux[0] = 0;
+            h->aux[4] = 0;
             h->done_counter = 0;
             atomicExch(&h->epoch, (epoch + 1u) & 0x3FFFFFFFu);
         }
@@ -744,23 +771,27 @@ static int g_blocklane_sumw = 0;
 
 void set_bp128_blocklane_sumw(int v) { g_blocklane_sumw = (v > 0 && v < bl::kW) ? v : 0; }
 
-// Scratch layout of a decode of n integers inside workspace h.
-static bl::Scratch blocklane_scratch(WsHeader* h, size_t n) {
-    const size_t nb = n / 128, M = (nb + 15) / 16, P = (M + 1) / 2;
-    unsigned long long* base =
-        reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h) + ws_unitmeta_end(n));
+// Scratch layout of a decode of n integers inside a workspace of ws_bytes
+// bytes at h: the last ws_blocklane_bytes(n) bytes (from a 256-byte
+// boundary).  Every region another decoder writes for a length m ends at
+// ws_unitmeta_end(m) <= ws_bytes - ws_blocklane_bytes(m), and the region
+// grows with the length, so no decoder sharing the workspace writes here.
+static bl::Scratch blocklane_scratch(WsHeader* h, size_t n, size_t ws_bytes) {
+    const size_t nb = n / 128, M = (nb + 15) / 16, P = (M + 1) / 2, Gn = (P + bl::kGroup - 1) / bl::kGroup;
+    const size_t at = (ws_bytes - ws_blocklane_bytes(n)) / 256 * 256;
+    unsigned long long* base = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h) + at);
     bl::Scratch sc;
     sc.bst = base;
     sc.ptot = sc.bst + 4 * (nb + 1);
     sc.pre = sc.ptot + 4 * (P + 1);
     sc.gst = sc.pre + 4 * (P + 1);
-    sc.gcnt = reinterpret_cast<unsigned int*>(sc.gst + 4 * ((P + bl::kGroup - 1) / bl::kGroup + 1));
+    sc.gcnt = reinterpret_cast<unsigned int*>(sc.gst + 4 * (Gn + 1));
     return sc;
 }
 
 template <int DELTA, int STORE>
 static cudaError_t launch_blocklane_t(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                      const uint64_t* index, WsHeader* h, cudaStream_t s) {
+                                      const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s) {
     auto kern = bp128_blocklane_kernel<DELTA, STORE>;
     const int smem = (int)(bl::kHdr + (size_t)bl::kW * bl::kWarpSmem);
     static int blocks_per_sm = -1;
@@ -780,7 +811,7 @@ static cudaError_t launch_blocklane_t(const uint8_t* in, size_t in_bytes, uint32
     size_t G = max((size_t)1, min(resident, (P + bl::kW - 1) / bl::kW));
     if (g_blocklane_ctas > 0 && (size_t)g_blocklane_ctas < G) G = (size_t)g_blocklane_ctas;
     const size_t lead = max((size_t)128, g_blocklane_lead > 0 ? (size_t)g_blocklane_lead : 2 * G * bl::kW);
-    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, h, blocklane_scratch(h, n),
+    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, h, blocklane_scratch(h, n, ws_bytes),
                                             (uint32_t)(n - 128 * nb), (uint32_t)min(lead, (size_t)0xFFFFFFFFu),
                                             (uint32_t)g_blocklane_sumw);
     return cudaGetLastError();
@@ -788,18 +819,18 @@ static cudaError_t launch_blocklane_t(const uint8_t* in, size_t in_bytes, uint32
 
 template <int DELTA>
 static cudaError_t launch_blocklane_d(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                      const uint64_t* index, WsHeader* h, cudaStream_t s) {
+                                      const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s) {
     int st = g_blocklane_store;
     if (st == bl::kStoreV8 && (reinterpret_cast<uintptr_t>(out) & 31u) != 0) st = bl::kStoreV4;
-    if (st == bl::kStoreRestage) return launch_blocklane_t<DELTA, bl::kStoreRestage>(in, in_bytes, out, n, index, h, s);
-    if (st == bl::kStoreV8) return launch_blocklane_t<DELTA, bl::kStoreV8>(in, in_bytes, out, n, index, h, s);
-    return launch_blocklane_t<DELTA, bl::kStoreV4>(in, in_bytes, out, n, index, h, s);
+    if (st == bl::kStoreRestage) return launch_blocklane_t<DELTA, bl::kStoreRestage>(in, in_bytes, out, n, index, h, ws_bytes, s);
+    if (st == bl::kStoreV8) return launch_blocklane_t<DELTA, bl::kStoreV8>(in, in_bytes, out, n, index, h, ws_bytes, s);
+    return launch_blocklane_t<DELTA, bl::kStoreV4>(in, in_bytes, out, n, index, h, ws_bytes, s);
 }
 
 cudaError_t launch_bp128_blocklane(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                   const uint64_t* index, WsHeader* h, cudaStream_t s) {
-    if (delta == ICX_DELTA_4) return launch_blocklane_d<ICX_DELTA_4>(in, in_bytes, out, n, index, h, s);
-    if (delta == ICX_DELTA_1) return launch_blocklane_d<ICX_DELTA_1>(in, in_bytes, out, n, index, h, s);
+                                   const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s) {
+    if (delta == ICX_DELTA_4) return launch_blocklane_d<ICX_DELTA_4>(in, in_bytes, out, n, index, h, ws_bytes, s);
+    if (delta == ICX_DELTA_1) return launch_blocklane_d<ICX_DELTA_1>(in, in_bytes, out, n, index, h, ws_bytes, s);
     return cudaErrorInvalidValue;
 }
 

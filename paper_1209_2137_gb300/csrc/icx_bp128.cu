@@ -319,9 +319,9 @@ static bool g_bp128_blocklane = true;  // two-phase block-per-lane decoder for t
 void set_bp128_blocklane(int on) { g_bp128_blocklane = on != 0; }
 
 cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
-                                size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s) {
+                                size_t n, const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s) {
     if (g_bp128_blocklane && fmt == ICX_FMT_PAPER && delta != ICX_DELTA_NONE)
-        return launch_bp128_blocklane(delta, in, in_bytes, out, n, index, h, s);
+        return launch_bp128_blocklane(delta, in, in_bytes, out, n, index, h, ws_bytes, s);
     return launch_bp128_decode_lookback(delta, fmt, in, in_bytes, out, n, index, h, s);
 }
 

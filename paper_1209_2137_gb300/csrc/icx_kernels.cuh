@@ -7,11 +7,11 @@
 namespace icx {
 
 cudaError_t launch_bp128_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
-                                size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s);
+                                size_t n, const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_bp128_decode_lookback(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out,
                                          size_t n, const uint64_t* index, WsHeader* h, cudaStream_t s);
 cudaError_t launch_bp128_blocklane(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                   const uint64_t* index, WsHeader* h, cudaStream_t s);
+                                   const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_bp128_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
                                WsHeader* h, cudaStream_t s);
 cudaError_t launch_delta_decode(int delta, const uint32_t* in, uint32_t* out, size_t n, WsHeader* h,

@@ -23,21 +23,34 @@ __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_ptr[kMaxDevices] = {nullptr};
+// Calls per device since the array was last zeroed: its look-back states are
+// tagged with a 30-bit launch number, so it is zeroed again (a memset, no
+// allocation) before 2^30 launches could reuse a tag.
+uint64_t g_calls[kMaxDevices] = {0};
+constexpr uint64_t kCallsPerZero = (uint64_t)1 << 29;
 
 // Device address of g_static_ws on the current device.  In host code the
 // symbol's name is only a host-side stand-in, so the address is looked up
-// once per device with cudaGetSymbolAddress (with that device current).
-icx_status static_workspace(void** out) {
+// with cudaGetSymbolAddress (with that device current) on every call made
+// outside stream capture -- after a device reset the module is loaded again
+// and the array may sit elsewhere -- and remembered per device for calls made
+// while `s` is being captured, when the lookup cannot run.
+icx_status static_workspace(cudaStream_t s, void** out, bool* rezero) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ICX_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return ICX_EINVAL;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return ICX_ECUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return ICX_ECUDA;
         g_ptr[dev] = p;
+    } else if (!g_ptr[dev]) {
+        return ICX_EINVAL;  // no call on this device was made before the capture
     }
     *out = g_ptr[dev];
+    *rezero = ++g_calls[dev] % kCallsPerZero == 0;
     return ICX_OK;
 }
 
@@ -57,10 +70,12 @@ extern "C" icx_status bp128_decode_static(const uint8_t* d_in, size_t in_bytes, 
     const size_t M = (n / 128 + 15) / 16;
     if (!d_index && M > 1) return ICX_EINVAL;
     void* ws = nullptr;
-    const icx_status st = static_workspace(&ws);
+    bool rezero = false;
+    const icx_status st = static_workspace((cudaStream_t)stream, &ws, &rezero);
     if (st != ICX_OK) return st;
     icx::WsHeader* h = static_cast<icx::WsHeader*>(ws);
     cudaStream_t s = (cudaStream_t)stream;
+    if (rezero && cudaMemsetAsync(ws, 0, kStaticBytes, s) != cudaSuccess) return ICX_ECUDA;
     // The array keeps the previous call's contents: the unit counters and
     // look-back states reset themselves at the end of every launch (epoch
     // tags), only the status word has to be cleared here.

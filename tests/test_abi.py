@@ -130,3 +130,22 @@ def test_layout_and_consumer_argument_checks(lib):
     # size helpers of the new layouts
     assert icx.bp128_max_bytes(1 << 20, icx.FMT_BP32) >= (1 << 20) // 128 * 516
     assert L.icx_fastpfor_max_bytes(1 << 20) >= (1 << 20) // 128 * (512 + 131 + 1024)
+
+
+def test_static_decode_refusals_before_any_device_call(lib):
+    # the allocation-free entry point checks its arguments on the host and
+    # returns before touching the device or its static workspace
+    import paper_1209_2137_gb300 as icx
+    fn = icx.lib().bp128_decode_static
+    vp, sz, i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    fn.argtypes = [vp, sz, vp, sz, i, i, vp, vp, vp]
+    fn.restype = i
+    a16, a4 = vp(4096), vp(4100)
+    assert fn(a16, 64, a16, 128, icx.DELTA_1, icx.FMT_SIMPLE8B, None, None, None) == icx.EINVAL  # not a BP128 layout
+    assert fn(a16, 64, a16, 128, 2, icx.FMT_PAPER, None, None, None) == icx.EINVAL  # no stride 2
+    assert fn(a4, 64, a16, 128, icx.DELTA_1, icx.FMT_PAPER, None, None, None) == icx.EALIGN
+    assert fn(a16, 64, a4, 128, icx.DELTA_1, icx.FMT_W32, None, None, None) == icx.EALIGN
+    assert fn(a16, 64, a16, 128, icx.DELTA_1, icx.FMT_BP32, vp(4104), None, None) == icx.EALIGN
+    assert fn(a16, 1 << 20, a16, 2049 * 16, icx.DELTA_4, icx.FMT_PAPER, None, None, None) == icx.EINVAL  # M > 1, no index
+    assert fn(a16, 64, a16, (1 << 28) + 1, icx.DELTA_1, icx.FMT_PAPER, a16, None, None) == icx.ENOSPC
+    assert fn(None, 0, None, 0, icx.DELTA_1, icx.FMT_PAPER, None, None, None) == icx.OK  # nothing to decode

@@ -101,3 +101,23 @@ def test_blocklane_variants_match_oracle(streams):
         icx.set_tuning("bp128.blocklane_store", -1)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane_lead", 0)
+
+
+def test_workspace_shared_by_decoders_of_different_lengths():
+    # one workspace serves SIMD-FastPFOR and SIMD-BP128* decodes of different
+    # lengths in turn (as the batched plan's one-call-per-list baseline does):
+    # the regions one decoder writes must not disturb the other's next launch
+    xs = [W.uniform_sorted(n, 28, 300 + n % 89) for n in (70_000, 300_000 + 77, 9_000, 150_000)]
+    ws = icx.Workspace(max(x.size for x in xs))
+    for _ in range(2):
+        for i, x in enumerate(xs):
+            for codec, delta in (("fastpfor", 1), ("bp128", 4), ("bp128", 1)):
+                enc = oracle.encode(codec, x, delta, 0)
+                d = torch.from_numpy(enc).cuda()
+                ix = torch.from_numpy(oracle.index(codec, enc, x.size, 0).view(np.int64)).cuda().view(torch.uint64)
+                if codec == "bp128":
+                    y = icx.bp128_decode(d, x.size, delta, 0, ix, workspace=ws)
+                else:
+                    y = icx.fastpfor_decode(d, x.size, delta, ix, workspace=ws)
+                assert ws.status() == icx.OK, (i, codec, delta)
+                assert np.array_equal(y.cpu().numpy().view(np.uint32), x), (i, codec, delta)
