@@ -266,7 +266,20 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *   "bp128.l2_prefetch" = 1 (default) / 0: each warp prefetches into L2 the
  *       metablock one grid of tiles ahead;
  *   "fastpfor.warps_per_cta" = 4 or 8 warps per CTA tile of the
- *       SIMD-FastPFOR decoder (0 = default: 4 for SIMD-FastPFOR stride 4, 8 otherwise).
+ *       SIMD-FastPFOR decoder (0 = default: 4 for SIMD-FastPFOR stride 4, 8 otherwise);
+ *   "bp128.blocklane" / "fastpfor.blocklane" = 1 / 0: decode the paper
+ *       layout with stride 1 or 4 in two passes with one block per lane (0:
+ *       the single-pass tile decoder with a chained look-back); default 1 for
+ *       SIMD-BP128, stride 1 only for SIMD-FastPFOR (-1 restores that);
+ *   "bp128.blocklane_store" = 0 (default: through shared memory, coalesced
+ *       16-byte stores), 1 (32-byte stores per lane), 2 (16-byte stores per
+ *       lane): output path of the two-pass decoders;
+ *   "bp128.blocklane_ctas" = CTAs of their persistent grid (0 = all resident);
+ *   "bp128.blocklane_lead" = pairs summed before the first decode task
+ *       (0 = two per resident warp; at least 128);
+ *   "bp128.blocklane_sum_warps" = warps per CTA that only sum (0 = every
+ *       warp takes both kinds of task).
+ * The bp128.blocklane_* settings apply to both two-pass decoders.
  * Takes effect for later launches; not thread safe against concurrent
  * launches.  ICX_EINVAL for an unknown key. */
 icx_status icx_set_tuning(const char *key, int value);

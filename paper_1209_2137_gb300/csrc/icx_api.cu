@@ -214,7 +214,7 @@ icx_status fastpfor_decode(const uint8_t* d_in, size_t in_bytes, uint32_t* d_out
         if (st != ICX_OK) return st;
         d_index = h->mini_index;
     }
-    return from_cuda(icx::launch_fastpfor_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, s));
+    return from_cuda(icx::launch_fastpfor_decode(delta, fmt, d_in, in_bytes, d_out, n, d_index, h, ws_bytes, s));
 }
 
 icx_status fastpfor_encode(const uint32_t* d_x, size_t n, icx_delta delta, icx_layout fmt, uint8_t* d_out,
@@ -242,6 +242,10 @@ icx_status icx_set_tuning(const char* key, int value) {
     }
     if (!strcmp(key, "bp128.blocklane")) {
         icx::set_bp128_blocklane(value);
+        return ICX_OK;
+    }
+    if (!strcmp(key, "fastpfor.blocklane")) {
+        icx::set_fastpfor_blocklane(value);
         return ICX_OK;
     }
     if (!strcmp(key, "bp128.blocklane_store")) {

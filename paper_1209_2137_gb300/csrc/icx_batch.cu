@@ -978,7 +978,8 @@ icx_status icx_plan_launch_per_list(icx_plan* p, icx_stream_t stream) {
                 le = launch_bp128_decode(l.delta, l.fmt, l.d_in, l.in_bytes, l.d_out, l.n, index, h,
                                          p->single_ws_bytes, p->cap);
             else
-                le = launch_fastpfor_decode(l.delta, ICX_FMT_PAPER, l.d_in, l.in_bytes, l.d_out, l.n, index, h, p->cap);
+                le = launch_fastpfor_decode(l.delta, ICX_FMT_PAPER, l.d_in, l.in_bytes, l.d_out, l.n, index, h,
+                                           p->single_ws_bytes, p->cap);
         }
         cudaError_t e = cudaStreamEndCapture(p->cap, &g);
         if (le != cudaSuccess) e = le;

@@ -458,9 +458,16 @@ cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, 
     return cudaGetLastError();
 }
 
+// Block-per-lane decoder for the SIMD layout with deltas: 1 = stride 1 and
+// 4, 0 = neither; -1 (default) = stride 1 only (measured on the 2^26 sorted
+// arrays: stride 1 0.167 vs 0.178 ms, stride 4 0.197 vs 0.178 ms).
+static int g_fp_blocklane = -1;
+
+void set_fastpfor_blocklane(int on) { g_fp_blocklane = on < 0 ? -1 : on != 0; }
+
 template <int DELTA, int W, int LAYOUT>
 static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
-                             WsHeader* h, cudaStream_t s) {
+                             WsHeader* h, size_t ws_bytes, cudaStream_t s) {
     void (*kern)(const uint8_t*, size_t, uint32_t*, size_t, const uint64_t*, const BlockMeta*, const uint32_t*,
                  const uint2*, WsHeader*);
     auto meta_kern = LAYOUT == ICX_FMT_SCALAR ? fastpfor_scalar_meta_kernel
@@ -503,6 +510,12 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
     if (P > 0) {
         meta_kern<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
     }
+    if (LAYOUT == ICX_FMT_PAPER && DELTA != ICX_DELTA_NONE &&
+        (g_fp_blocklane > 0 || (g_fp_blocklane < 0 && DELTA == ICX_DELTA_1))) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_fastpfor_blocklane(DELTA, in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);
+    }
     const size_t ntiles = (U + 1 + W - 1) / W;
     const int grid = (int)min((size_t)blocks_per_sm * sms, ntiles);
     kern<<<grid, W * 32, smem, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, h);
@@ -515,20 +528,20 @@ void set_fastpfor_warps(int w) { g_fp_warps = (w == 4 || w == 8) ? w : 0; }
 
 template <int DELTA, int LAYOUT>
 static cudaError_t launch_fp_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
-                               WsHeader* h, cudaStream_t s) {
+                               WsHeader* h, size_t ws_bytes, cudaStream_t s) {
     // measured on the 2^26 sorted arrays: 4 warps per CTA for the pipelined
     // SIMD-FastPFOR stride-4 kernel (0.1816 vs 0.1820 ms), 8 for the others
     // (SIMD stride 1: 0.178 vs 0.181 ms; scalar FastPFOR and SimplePFOR
     // stride 4: 0.183 vs 0.198 and 0.197 vs 0.207 ms)
     const int w = g_fp_warps ? g_fp_warps : (DELTA == ICX_DELTA_4 && LAYOUT == ICX_FMT_PAPER ? 4 : 8);
-    if (w == 4) return launch_fp<DELTA, 4, LAYOUT>(in, in_bytes, out, n, index, h, s);
-    return launch_fp<DELTA, 8, LAYOUT>(in, in_bytes, out, n, index, h, s);
+    if (w == 4) return launch_fp<DELTA, 4, LAYOUT>(in, in_bytes, out, n, index, h, ws_bytes, s);
+    return launch_fp<DELTA, 8, LAYOUT>(in, in_bytes, out, n, index, h, ws_bytes, s);
 }
 
 cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                   const uint64_t* index, WsHeader* h, cudaStream_t s) {
+                                   const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s) {
 #define ICX_CASE(D, L) \
-    if (delta == D && fmt == L) return launch_fp_w<D, L>(in, in_bytes, out, n, index, h, s);
+    if (delta == D && fmt == L) return launch_fp_w<D, L>(in, in_bytes, out, n, index, h, ws_bytes, s);
     ICX_CASE(ICX_DELTA_NONE, ICX_FMT_PAPER)
     ICX_CASE(ICX_DELTA_1, ICX_FMT_PAPER)
     ICX_CASE(ICX_DELTA_4, ICX_FMT_PAPER)

@@ -20,7 +20,10 @@ cudaError_t launch_delta_encode(int delta, const uint32_t* x, uint32_t* d, size_
 cudaError_t launch_bp128_encode(int delta, int fmt, const uint32_t* x, size_t n, uint8_t* out, uint64_t* index,
                                 uint64_t* out_bytes, uint8_t* widths, uint32_t* sizes, cudaStream_t s);
 cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
-                                   const uint64_t* index, WsHeader* h, cudaStream_t s);
+                                   const uint64_t* index, WsHeader* h, size_t ws_bytes, cudaStream_t s);
+cudaError_t launch_fastpfor_blocklane(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                      const uint64_t* index, const BlockMeta* meta, const uint32_t* pmeta,
+                                      const uint2* umeta, WsHeader* h, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
                                   WsHeader* h, cudaStream_t s);
 cudaError_t launch_fastpfor_encode(int delta, int fmt, const uint32_t* x, size_t n, uint8_t* out, size_t out_cap,
@@ -41,5 +44,6 @@ void set_bp128_blocklane_ctas(int v);
 void set_bp128_blocklane_lead(int v);
 void set_bp128_blocklane_sumw(int v);
 void set_fastpfor_warps(int w);
+void set_fastpfor_blocklane(int on);
 
 }  // namespace icx

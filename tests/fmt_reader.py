@@ -52,17 +52,21 @@ def fastpfor_walk(buf, n, chunk=128):
         L = le32(buf, base + len_at)
         rec_at = base + len_at + 4
         records = []
+        pos_at = []  # stream offset of each block's first position (None: no exceptions)
         r = 0
         for _ in range(k):
             b, mb = buf[rec_at + r], buf[rec_at + r + 1]
             r += 2
             pos_list = []
+            at = None
             if mb > b:
                 c = buf[rec_at + r]
                 r += 1
+                at = rec_at + r
                 pos_list = list(buf[rec_at + r:rec_at + r + c])
                 r += c
             records.append((b, mb, pos_list))
+            pos_at.append(at)
         assert r == L, (r, L)
         q = rec_at + pad(L, 4)
         bitset = le32(buf, q)
@@ -76,7 +80,7 @@ def fastpfor_walk(buf, n, chunk=128):
                 q += chunk // 8 * d * ((cnt + chunk - 1) // chunk)
         end = base + pad(q - base, 16)
         pages.append(dict(offset=base, blocks=k, len_at=len_at, byte_len=L, records=records,
-                          bitset=bitset, arrays=arrays, size=end - base))
+                          bitset=bitset, arrays=arrays, size=end - base, pos_at=pos_at))
         pos = end
     return pages, pos
 

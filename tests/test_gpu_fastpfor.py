@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_1209_2137_gb300 import workloads as W
+from tests import fmt_reader as F
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -143,3 +144,80 @@ def test_fastpfor_full_size_sorted(delta):
     ws = icx.Workspace(x.size)
     y = host_u32(icx.decode(enc, workspace=ws))
     assert ws.status() == icx.OK and np.array_equal(y, x)
+
+
+def _blocks_with_exceptions(enc, n, at_least):
+    """(block index, stream offset of its positions, count) of every block
+    with at least `at_least` exceptions."""
+    pages, _ = F.fastpfor_walk(enc, n)
+    out = []
+    for p, pg in enumerate(pages):
+        for k, ((b, mb, pos), at) in enumerate(zip(pg["records"], pg["pos_at"])):
+            if at is not None and len(pos) >= at_least:
+                out.append((512 * p + k, at, len(pos)))
+    return out
+
+
+@pytest.mark.parametrize("delta", [icx.DELTA_1, icx.DELTA_4])
+def test_fastpfor_positions_out_of_order(delta):
+    # The format stores a block's exception positions as a list; the encoder
+    # writes them in increasing order, but any order (and a repeated
+    # position, whose high parts are OR-ed) decodes by the same patch rule
+    # (Sec. 5).  Blocks with reversed, swapped and repeated positions, alone
+    # in their warp's pair and filling a whole pair, against the oracle.
+    n = 2 * PAGE + 4096 * 3 + 77
+    x = W.uniform_sorted(n, 29, 64)
+    enc = oracle.fastpfor_encode(x, delta).copy()
+    blocks = _blocks_with_exceptions(enc, n, 3)
+    assert len(blocks) > 200
+    chosen = {}
+    for blk, at, c in blocks:
+        chosen.setdefault(blk // 32, []).append((blk, at, c))
+    pairs = sorted(chosen)
+    edits = 0
+    # one edited block in each of a few pairs, a different edit each time
+    for i, pr in enumerate(pairs[1:40:6]):
+        blk, at, c = chosen[pr][0]
+        seg = enc[at:at + c].copy()
+        if i % 4 == 0:
+            enc[at:at + c] = seg[::-1]  # reversed
+        elif i % 4 == 1:
+            enc[at + 1] = seg[0]  # a repeated position next to the first
+        elif i % 4 == 2:
+            enc[at + c - 1] = seg[0]  # the last equals the first
+        else:
+            enc[at], enc[at + 1] = seg[1], seg[0]  # first two swapped
+        edits += 1
+    # every block of one pair reversed
+    for blk, at, c in chosen[pairs[-2]]:
+        enc[at:at + c] = enc[at:at + c][::-1].copy()
+        edits += 1
+    assert edits > 8
+    want = oracle.fastpfor_decode(enc, n, delta)
+    assert want.size == n
+    y, st = gpu_decode(enc, n, delta)
+    assert st == icx.OK
+    assert np.array_equal(y, want), int(np.argmax(y != want))
+    # and the same stream through both decoders
+    for mode in (1, 0):
+        icx.set_tuning("fastpfor.blocklane", mode)
+        try:
+            y0, st0 = gpu_decode(enc, n, delta)
+        finally:
+            icx.set_tuning("fastpfor.blocklane", -1)
+        assert st0 == icx.OK and np.array_equal(y0, want), mode
+
+
+@pytest.mark.parametrize("delta", [icx.DELTA_1, icx.DELTA_4])
+def test_fastpfor_position_past_the_block_is_corrupt(delta):
+    n = PAGE + 4096 + 5
+    x = W.uniform_sorted(n, 29, 65)
+    enc = oracle.fastpfor_encode(x, delta).copy()
+    idx = oracle.fastpfor_index(enc, n)  # the page sizes do not change
+    blk, at, c = _blocks_with_exceptions(enc, n, 2)[40]
+    enc[at + 1] = 200
+    with pytest.raises(oracle.CorruptStream):  # the oracle refuses the stream
+        oracle.fastpfor_decode(enc, n, delta)
+    ws = icx.Workspace(n)
+    icx.fastpfor_decode(dev(enc), n, delta, index=dev(idx), workspace=ws)
+    assert ws.status() == icx.ECORRUPT

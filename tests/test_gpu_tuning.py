@@ -62,42 +62,47 @@ def test_every_launch_variant_matches_oracle(streams):
 
 
 def test_blocklane_variants_match_oracle(streams):
-    """The two-phase block-per-lane decoder (paper layout, strides 1 and 4):
-    every output store path, grids of 1, 2 and 5 CTAs (a few warps take all
-    the tasks, group scans and the tail), the shortest and the longest lead
-    of sums before decodes, and the single-pass decoder it replaces."""
+    """The two-phase block-per-lane decoders (SIMD-BP128 and SIMD-FastPFOR,
+    strides 1 and 4): every output store path, grids of 1, 2 and 5 CTAs (a
+    few warps take all the tasks, group scans and the tail), the shortest and
+    the longest lead of sums before decodes, and the single-pass decoders
+    they replace."""
+    icx.set_tuning("fastpfor.blocklane", 1)
     try:
         for store in (0, 1, 2):
             icx.set_tuning("bp128.blocklane_store", store)
             for ctas in (0, 1, 2, 5):
                 icx.set_tuning("bp128.blocklane_ctas", ctas)
                 for codec, delta, fmt, enc, idx, want in streams:
-                    if codec == "bp128" and fmt == icx.FMT_PAPER:
-                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (store, ctas, delta)
+                    if fmt == icx.FMT_PAPER:
+                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (codec, store, ctas, delta)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane_store", -1)
         for lead in (128, 1 << 30):  # the shortest lead, and every sum before the first decode
             icx.set_tuning("bp128.blocklane_lead", lead)
             for codec, delta, fmt, enc, idx, want in streams:
-                if codec == "bp128" and fmt == icx.FMT_PAPER:
-                    assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("lead", lead, delta)
+                if fmt == icx.FMT_PAPER:
+                    assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (codec, "lead", lead, delta)
         icx.set_tuning("bp128.blocklane_lead", 0)
         for sumw in (1, 2, 5):  # warps specialised for summing and decoding
             icx.set_tuning("bp128.blocklane_sum_warps", sumw)
             for ctas in (0, 1):
                 icx.set_tuning("bp128.blocklane_ctas", ctas)
                 for codec, delta, fmt, enc, idx, want in streams:
-                    if codec == "bp128" and fmt == icx.FMT_PAPER:
-                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("sum warps", sumw, ctas)
+                    if fmt == icx.FMT_PAPER:
+                        assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (codec, "sum warps", sumw,
+                                                                                           ctas)
         icx.set_tuning("bp128.blocklane_sum_warps", 0)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane", 0)
+        icx.set_tuning("fastpfor.blocklane", 0)
         for codec, delta, fmt, enc, idx, want in streams:
-            if codec == "bp128" and fmt == icx.FMT_PAPER:
-                assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("single pass", delta)
+            if fmt == icx.FMT_PAPER:
+                assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (codec, "single pass", delta)
     finally:
         icx.set_tuning("bp128.blocklane_sum_warps", 0)
         icx.set_tuning("bp128.blocklane", 1)
+        icx.set_tuning("fastpfor.blocklane", -1)
         icx.set_tuning("bp128.blocklane_store", -1)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane_lead", 0)
