@@ -267,10 +267,13 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *       metablock one grid of tiles ahead;
  *   "fastpfor.warps_per_cta" = 4 or 8 warps per CTA tile of the
  *       SIMD-FastPFOR decoder (0 = default: 4 for SIMD-FastPFOR stride 4, 8 otherwise);
- *   "bp128.blocklane" / "fastpfor.blocklane" = 1 / 0: decode the paper
- *       layout with stride 1 or 4 in two passes with one block per lane (0:
- *       the single-pass tile decoder with a chained look-back); default 1 for
- *       SIMD-BP128, stride 1 only for SIMD-FastPFOR (-1 restores that);
+ *   "bp128.blocklane" = 1 (default) / 0: decode the paper layout with
+ *       stride 1 or 4 in two passes with one block per lane (0: the
+ *       single-pass tile decoder with a chained look-back);
+ *   "fastpfor.blocklane" = 2 (default): SIMD-FastPFOR with stride 1 or 4 by
+ *       a kernel that parses, sums and prepares every block and one that
+ *       streams the integers out; 1: one block-per-lane kernel after the page
+ *       parse; 0: the tile decoder with a chained look-back (-1 = default);
  *   "bp128.blocklane_store" = 0 (default: through shared memory, coalesced
  *       16-byte stores), 1 (32-byte stores per lane), 2 (16-byte stores per
  *       lane): output path of the two-pass decoders;

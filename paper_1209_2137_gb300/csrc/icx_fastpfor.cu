@@ -458,12 +458,12 @@ cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, 
     return cudaGetLastError();
 }
 
-// Block-per-lane decoder for the SIMD layout with deltas: 1 = stride 1 and
-// 4, 0 = neither; -1 (default) = stride 1 only (measured on the 2^26 sorted
-// arrays: stride 1 0.167 vs 0.178 ms, stride 4 0.197 vs 0.178 ms).
-static int g_fp_blocklane = -1;
+// Decoder of the SIMD layout with deltas: 0 = the tile decoder with a
+// chained look-back, 1 = the block-per-lane decoder (block sums as tasks of
+// the same kernel), 2 (default) = the prepare and stream kernels.
+static int g_fp_blocklane = 2;
 
-void set_fastpfor_blocklane(int on) { g_fp_blocklane = on < 0 ? -1 : on != 0; }
+void set_fastpfor_blocklane(int v) { g_fp_blocklane = v < 0 || v > 2 ? 2 : v; }
 
 template <int DELTA, int W, int LAYOUT>
 static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
@@ -507,11 +507,12 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
     uint32_t* pmeta = reinterpret_cast<uint32_t*>(ws + ws_pagemeta_off(n));
     uint2* umeta = reinterpret_cast<uint2*>(ws + ws_unitmeta_off(n));
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, U = (nb + 15) / 16;
+    if (LAYOUT == ICX_FMT_PAPER && DELTA != ICX_DELTA_NONE && g_fp_blocklane == 2)
+        return launch_fastpfor_two_kernel(DELTA, in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);
     if (P > 0) {
         meta_kern<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
     }
-    if (LAYOUT == ICX_FMT_PAPER && DELTA != ICX_DELTA_NONE &&
-        (g_fp_blocklane > 0 || (g_fp_blocklane < 0 && DELTA == ICX_DELTA_1))) {
+    if (LAYOUT == ICX_FMT_PAPER && DELTA != ICX_DELTA_NONE && g_fp_blocklane == 1) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return launch_fastpfor_blocklane(DELTA, in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);

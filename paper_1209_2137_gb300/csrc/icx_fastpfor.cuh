@@ -89,38 +89,36 @@ __device__ __forceinline__ uint64_t array_bytes(uint32_t d, uint32_t nd) {
 
 // Whole warp: the exception arrays after a page's byte array.  Their offsets
 // follow from the page's per-width counts (lane d-1 holds cnt_total of
-// width d); lane d-1 checks the stored count of array d against it, and the
-// arrays must end exactly at the page end.  Writes the page record pg (array
-// offsets, then the flag word) and returns the warp-uniform `bad`.
+// width d): after the bitset, each present width d has its stored count
+// (the first right after the bitset, the others 16-byte aligned) and then,
+// from the next 16-byte boundary, its array; so array d starts at the first
+// array's offset plus (16 + size) of every present width below d, one warp
+// scan.  Lane d-1 checks the stored count of array d against its total, and
+// the arrays must end exactly at the page end.  Writes the page record pg
+// (array offsets, then the flag word) and returns the warp-uniform `bad`.
 template <int LAYOUT>
 __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize, uint32_t bytes_at, uint32_t Lpad,
                                             uint32_t cnt_total, bool bad, uint32_t* __restrict__ pg, WsHeader* h,
                                             int lane) {
     uint32_t my_off = 0, my_cnt_at = 0;
+    bool present = false;
     if (!bad) {
         const uint32_t bitset = ld32(page + bytes_at + Lpad);
-        uint64_t q = (uint64_t)bytes_at + Lpad + 4;
-        for (int d = 1; d <= 32; ++d) {
-            const uint32_t nd = __shfl_sync(FULL, cnt_total, d - 1);
-            if (!((bitset >> (d - 1)) & 1u)) {
-                if (nd) bad = true;
-                continue;
-            }
-            if (lane == d - 1) {
-                my_cnt_at = (uint32_t)q;
-                my_off = (uint32_t)pad_up(q + 4, 16);
-            }
-            q = pad_up(q + 4, 16) + array_bytes<LAYOUT>(d, nd);
-            if (q > psize) {
-                bad = true;
-                break;
-            }
-        }
-        if (pad_up(q, 16) != psize) bad = true;
-        if (!bad && ((bitset >> lane) & 1u) && ld32(page + my_cnt_at) != cnt_total) bad = true;
+        present = (bitset >> lane) & 1u;
+        if (!present && cnt_total) bad = true;
+        const uint32_t sz = present ? 16u + (uint32_t)array_bytes<LAYOUT>(lane + 1, cnt_total) : 0u;
+        const uint32_t incl = warp_incl_scan(sz, lane), total = __shfl_sync(FULL, incl, 31);
+        const uint32_t q0 = bytes_at + Lpad + 4;  // the first stored count
+        const uint32_t p0 = (uint32_t)pad_up(q0 + 4, 16);  // the first array
+        my_off = p0 + incl - sz;
+        my_cnt_at = incl == sz ? q0 : my_off - 16;
+        const uint64_t q_end = total ? (uint64_t)p0 + total - 16 : (uint64_t)q0;
+        if (q_end > psize || pad_up(q_end, 16) != psize) bad = true;
     }
     bad = __any_sync(FULL, bad);
-    pg[lane] = bad ? 0u : my_off;
+    if (!bad && present && ld32(page + my_cnt_at) != cnt_total) bad = true;
+    bad = __any_sync(FULL, bad);
+    pg[lane] = bad || !present ? 0u : my_off;
     if (lane == 0) pg[32] = bad ? 1u : 0u;
     if (bad && lane == 0) set_error(h, ICX_ECORRUPT);
     return bad;
@@ -184,9 +182,10 @@ __device__ __forceinline__ uint32_t round_cursor(uint32_t d, uint32_t c, uint32_
 // Parses one page, CTA-wide (kMetaThreads threads): the page occupies
 // in[base, end) and holds K blocks; writes the K block records to pm, the
 // exception-array offsets and the page flag to pg, and per unit of 16
-// blocks its packed range to um.
+// blocks its packed range to um.  Returns true (in every thread) when the
+// page is corrupt.
 template <int LAYOUT = ICX_FMT_PAPER>
-__device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restrict__ in, size_t in_bytes,
+__device__ __forceinline__ bool parse_page(MetaSmem& S, const uint8_t* __restrict__ in, size_t in_bytes,
                                            uint64_t base, uint64_t end, uint32_t K, BlockMeta* __restrict__ pm,
                                            uint32_t* __restrict__ pg, uint2* __restrict__ um, WsHeader* h,
                                            ulonglong2* __restrict__ rng = nullptr) {
@@ -209,6 +208,13 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
     }
     const uint32_t Lpad = bad ? 0u : (uint32_t)pad_up(L, 4);
     const uint32_t* arr = reinterpret_cast<const uint32_t*>(page + bytes_at);  // 4-byte aligned
+    // what follows the byte array (bitset, counts, exception arrays) is read
+    // only at the end of the parse: start pulling it into L2 now
+    if (!bad && tid == 0) {
+        const uint32_t a0 = (bytes_at + Lpad) & ~15u;
+        const uint32_t nbytes = min(psize - a0, 65536u) & ~15u;
+        if (nbytes) prefetch_l2(page + a0, nbytes);
+    }
 
     // ---- record starts, one window of the byte array at a time
     if (LAYOUT == kSimple && tid < (int)kUnitsPerPage) S.uexc[tid] = 0xFFFFFFFFu;
@@ -227,20 +233,24 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         const uint32_t Lw = L - ws;  // > 0: the chain only continues at starts < L
         const uint32_t lim8 = min(kMetaWin, Lw), lim4 = lim8 + 4 * kRecMax, lim2 = lim4 + 2 * kRecMax;
         const uint32_t nw = ws < Lpad ? min(kMetaSpan / 4, (Lpad - ws) / 4) : 0u;
+#pragma unroll 4
         for (uint32_t i = tid; i < kMetaSpan / 4 + 4; i += kMetaThreads) S.bytes[i] = i < nw ? __ldg(arr + ws / 4 + i) : 0u;
         __syncthreads();
         // J2 straight from the bytes (i + a + 3 <= lim2 + kRecMax + 2 stays
         // inside the window's words)
+#pragma unroll 4
         for (uint32_t i = tid; i < lim2; i += kMetaThreads) {
             const uint32_t a = rec_len_at(S.bytes, i);
             S.ja[i] = (uint16_t)(a + rec_len_at(S.bytes, i + a));
         }
         __syncthreads();
+#pragma unroll 4
         for (uint32_t i = tid; i < lim4; i += kMetaThreads) {
             const uint32_t a = S.ja[i];
             S.jb[i] = (uint16_t)(a + S.ja[i + a]);
         }
         __syncthreads();
+#pragma unroll 4
         for (uint32_t i = tid; i < lim8; i += kMetaThreads) {
             const uint32_t a = S.jb[i];
             S.ja[i] = (uint16_t)(a + S.jb[i + a]);
@@ -403,6 +413,7 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
     } else {
         if (warp == 0) bad = page_arrays<LAYOUT>(page, psize, bytes_at, Lpad, cnt_total, bad, pg, h, lane);
         __syncthreads();
+        bad = *reinterpret_cast<volatile const uint32_t*>(pg + 32) != 0;
     }
     // per unit of 16 blocks: where its packed low bits start and how long they are
     const uint32_t nunits = (K + 15) / 16;
@@ -415,6 +426,7 @@ __device__ __forceinline__ void parse_page(MetaSmem& S, const uint8_t* __restric
         }
         if (rng) rng[tid] = make_ulonglong2(bad ? 0ull : reinterpret_cast<uint64_t>(page + x.x), x.y);
     }
+    return bad;
 }
 
 

@@ -1,0 +1,613 @@
+// SIMD-FastPFOR decoding fused with differential decoding (Sec. 5, Sec. 6.2)
+// in two kernels: one that prepares every block, one that streams the
+// decoded integers out.
+//
+//  1. fastpfor_prep_kernel, one CTA per page (in the order the CTAs start):
+//     parses the page's byte array (the record of every block), then per
+//     block (one thread each) sums its integers -- the low parts by walking
+//     its packed rows, plus high << b for each exception -- and leaves the
+//     block's exceptions for the second kernel in the pair's own output
+//     region: one 32-bit entry (position | high << 8) per exception, in
+//     position order.  A block whose exceptions cannot be written so (high
+//     parts wider than 24 bits, positions out of order or repeated) is
+//     decoded there completely instead, as its 128 differences (Sec. 5:
+//     every exception OR-ed in as high << b, in stream order).  The block
+//     sums are scanned across the page and across pages (decoupled
+//     look-back), and each block's carry (its exclusive prefix, Sec. 3) is
+//     written with its packed offset and entry offset.  The CTA of the last
+//     page also decodes the Variable Byte tail (Sec. 2.4).
+//  2. fastpfor_stream_kernel, persistent warps, one pair of 32 blocks per
+//     step: one bulk copy of the pair's packed low bits and one of its
+//     entries (or complete blocks) from its output region into shared
+//     memory; then lane L walks block L's fields from its carry as the
+//     SIMD-BP128 decoder does, ORs each entry into its field just before
+//     that field is emitted, and the fields are written through the
+//     restaging buffer.  A pair's output region is read before it is
+//     written, and by the warp that writes it.
+#include <cstddef>
+
+#include "icx_blocklane.cuh"
+#include "icx_fastpfor.cuh"
+#include "icx_kernels.cuh"
+
+namespace icx {
+
+namespace fp2 {
+
+constexpr uint32_t kPairsPerPage = kBlocksPerPage / 32;
+constexpr uint32_t kHighMax = 24;    // widest high part an entry holds
+constexpr uint32_t kRaw = 1u << 31;  // record: the block's area holds its 128 differences
+constexpr uint32_t kDirect = 1u << 30;  // record: the block is decoded by the prepare kernel
+constexpr uint32_t kBad = 1u << 16;  // record: the block's page is corrupt
+
+// One thread's block in the prepare kernel: high part j of its exceptions
+// (element cur + j of the page's array of width d at arr).
+__device__ __forceinline__ uint32_t high_part(const uint8_t* arr, uint32_t e, uint32_t d) {
+    const uint32_t i = e & 127, bit = (i >> 2) * d;
+    const uint8_t* w = arr + 16 * (size_t)d * (e >> 7) + 16 * (bit >> 5) + 4 * (i & 3);
+    const uint32_t s = bit & 31;
+    const uint32_t lo = ld32(w), hi = s + d > 32 ? ld32(w + 16) : 0u;
+    return __funnelshift_r(lo, hi, s) & width_mask(d);
+}
+
+// Rows of the stream read with predicated loads, so that threads of one warp
+// whose windows move at different fields do not diverge; a row past `avail`
+// reads as zeros.
+struct PredRows {
+    const uint8_t* base;
+    uint64_t avail;
+    __device__ __forceinline__ uint4 operator()(uint32_t off) const {
+        return (uint64_t)off + 16 <= avail ? __ldg(reinterpret_cast<const uint4*>(base + off)) : make_uint4(0, 0, 0, 0);
+    }
+    __device__ __forceinline__ uint32_t cursor(uint32_t off) const { return off; }
+    __device__ __forceinline__ void advance(uint4& r0, uint4& r1, uint32_t& sh, uint32_t& nxt) const {
+        const bool p = sh >= 32;
+        uint4 r2 = r1;
+        if (p && (uint64_t)nxt + 16 <= avail) r2 = __ldg(reinterpret_cast<const uint4*>(base + nxt));
+        else if (p) r2 = make_uint4(0, 0, 0, 0);
+        r0 = p ? r1 : r0;
+        r1 = r2;
+        nxt += p ? 16u : 0u;
+        sh &= 31;
+    }
+};
+
+struct NoMid {
+    __device__ __forceinline__ void operator()() {}
+};
+
+}  // namespace fp2
+
+// ------------------------------------------------------------------ kernel 1
+
+template <int DELTA>
+__global__ void __launch_bounds__(kMetaThreads, 7)
+    fastpfor_prep_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
+                         const uint64_t* __restrict__ index, BlockMeta* __restrict__ meta,
+                         uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta, uint4* __restrict__ rec,
+                         WsHeader* h, uint32_t tail) {
+    using namespace fp2;
+    using namespace bl;
+    constexpr int NL = DELTA == ICX_DELTA_4 ? 4 : 1;
+    __shared__ MetaSmem S;
+    __shared__ uint4 wtot[kMetaThreads / 32];
+    __shared__ uint4 page_pre;
+    __shared__ uint32_t arr_s[32];
+    __shared__ uint32_t pid_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t epoch = launch_epoch(h);
+    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
+    if (tid == 0) pid_s = atomicAdd(&h->tile_counter, 1u);
+    __syncthreads();
+    const uint32_t p = pid_s;
+    uint4 incl_all = make_uint4(0, 0, 0, 0);  // inclusive prefix through this page
+    if (p < P) {
+        const uint32_t K = (uint32_t)min((size_t)kBlocksPerPage, nb - kBlocksPerPage * (size_t)p);
+        const uint64_t base = __ldg(index + p), end = __ldg(index + p + 1);
+        BlockMeta* pm = meta + kBlocksPerPage * (size_t)p;
+        uint32_t* pg = pmeta + kPageMetaWords * (size_t)p;
+        const bool bad = parse_page<ICX_FMT_PAPER>(S, in, in_bytes, base, end, K, pm, pg,
+                                                   umeta + kUnitsPerPage * (size_t)p, h);
+        if (tid < 32) arr_s[tid] = bad ? 0u : __ldcg(pg + tid);
+        __syncthreads();
+        // the jump tables are free now: block sums and area offsets
+        uint4* sums = reinterpret_cast<uint4*>(S.ja);
+        uint16_t* area_s = S.jb;
+        static_assert(sizeof(S.ja) >= kBlocksPerPage * sizeof(uint4), "block sums fit the jump table");
+        const uint8_t* page = in + base;
+        // ---- per block: its sum, its entries (or its differences)
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t k = 128 * warp + 32 * i + lane;
+            const bool valid = !bad && k < K;
+            uint32_t b = 0, d = 0, c = 0, pk = 0, po = 0, cur = 0;
+            if (valid) {
+                const uint4 m = __ldcg(reinterpret_cast<const uint4*>(pm + k));
+                pk = m.x;
+                po = m.y;
+                cur = m.z;
+                b = m.w & 0xFF;
+                d = (m.w >> 8) & 0xFF;
+                c = d ? (m.w >> 16) & 0xFF : 0u;
+            }
+            // exceptions that an entry cannot hold make the block raw
+            bool raw = d > kHighMax, corrupt = false;
+            {
+                uint32_t prev = 0;
+                for (uint32_t j = 0; j < c; ++j) {
+                    const uint32_t q = __ldg(page + po + j);
+                    corrupt |= q >= 128;
+                    if (q >= 128 || (j && q <= prev)) raw = true;
+                    prev = q;
+                }
+            }
+            if (__any_sync(FULL, corrupt) && lane == 0) set_error(h, ICX_ECORRUPT);
+            // a pair whose packed bits and area do not fit the decoder's
+            // staging slot is decoded here, every block in its own output
+            uint32_t E = !valid ? 0u : raw ? 128u : c;
+            const uint32_t Sp = __reduce_add_sync(FULL, 16 * b);
+            const bool direct = Sp + ((4 * __reduce_add_sync(FULL, E) + 15) & ~15u) > kRing;
+            if (direct) E = 0;
+            const uint32_t eincl = warp_incl_scan(E, lane);
+            const uint32_t ent = eincl - E;
+            uint32_t* area = direct ? out + 128 * (kBlocksPerPage * (size_t)p + k)
+                                    : out + 4096 * ((size_t)kPairsPerPage * p + 4 * warp + i) + ent;
+            // the low parts' sum: the block's fields, walked like the decoder
+            Walk w;
+            w.b = b;
+            w.mask = width_mask(b);
+            const PredRows rows{page, in_bytes - base};
+            w.r0 = valid ? rows(pk) : make_uint4(0, 0, 0, 0);
+            w.r1 = valid ? rows(pk + 16) : make_uint4(0, 0, 0, 0);
+            w.nxt = pk + 32;
+            w.sh = 0;
+            w.acc = make_uint4(0, 0, 0, 0);
+            const uint32_t maxb = __reduce_max_sync(FULL, b);
+            NoPatch np;
+            NoMid nm;
+            if (maxb && __any_sync(FULL, valid && !raw && !direct)) {
+                const PredRows rr{valid ? page : in, valid ? in_bytes - base : 0};
+                if (maxb <= 8)
+                    walk_block<DELTA, false, 0, 4>(rr, w, nm, np);
+                else if (maxb <= 16)
+                    walk_block<DELTA, false, 0, 2>(rr, w, nm, np);
+                else
+                    walk_block<DELTA, false, 0, 1>(rr, w, nm, np);
+            }
+            uint4 s = w.acc;
+            const uint8_t* arr = page + arr_s[d ? d - 1 : 0];
+            if (valid && !raw && !direct) {
+                for (uint32_t j = 0; j < c; ++j) {
+                    const uint32_t q = __ldg(page + po + j);
+                    const uint32_t hv = high_part(arr, cur + j, d);
+                    area[j] = q | hv << 8;
+                    const uint32_t x = hv << b;
+                    s.x += (q & 3) == 0 ? x : 0u;
+                    s.y += (q & 3) == 1 ? x : 0u;
+                    s.z += (q & 3) == 2 ? x : 0u;
+                    s.w += (q & 3) == 3 ? x : 0u;
+                }
+            } else if (valid) {
+                // the 128 differences: low parts, then every exception OR-ed in
+                const uint32_t mask = width_mask(b);
+                for (uint32_t r = 0; r < 32; ++r) {
+                    const uint32_t bit = r * b, wo = 16 * (bit >> 5), sh = bit & 31;
+                    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                    if (b) {
+                        lo = rows(pk + wo);
+                        if (sh + b > 32) hi = rows(pk + wo + 16);
+                    }
+                    *reinterpret_cast<uint4*>(area + 4 * r) =
+                        make_uint4(__funnelshift_r(lo.x, hi.x, sh) & mask, __funnelshift_r(lo.y, hi.y, sh) & mask,
+                                   __funnelshift_r(lo.z, hi.z, sh) & mask, __funnelshift_r(lo.w, hi.w, sh) & mask);
+                }
+                for (uint32_t j = 0; j < c; ++j) {
+                    const uint32_t q = __ldg(page + po + j);
+                    if (q < 128) area[q] |= high_part(arr, cur + j, d) << b;
+                }
+                s = make_uint4(0, 0, 0, 0);
+                for (uint32_t r = 0; r < 32; ++r) s = add4(s, *reinterpret_cast<const uint4*>(area + 4 * r));
+            }
+            if (k < K) {
+                sums[k] = DELTA == ICX_DELTA_4 ? s : make_uint4(s.x + s.y + s.z + s.w, 0, 0, 0);
+                area_s[k] = (uint16_t)(ent | (raw ? 0x8000u : 0u) | (direct ? 0x4000u : 0u));
+            }
+        }
+        __syncthreads();
+        // ---- the page's scan: thread t takes blocks 4t .. 4t+3
+        uint4 v[4], run = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t kk = 4 * tid + r;
+            v[r] = kk < K ? sums[kk] : make_uint4(0, 0, 0, 0);
+            run = add4(run, v[r]);
+        }
+        const uint4 ti = warp_scan_carry<DELTA>(run, lane);
+        if (lane == 31) wtot[warp] = ti;
+        __syncthreads();
+        uint4 woff = make_uint4(0, 0, 0, 0), tot = woff;
+#pragma unroll
+        for (int ww = 0; ww < kMetaThreads / 32; ++ww) {
+            if (ww < warp) woff = add4(woff, wtot[ww]);
+            tot = add4(tot, wtot[ww]);
+        }
+        if (warp == 0) {
+            const uint4 ex = lookback<NL>(h, epoch, p, tot);
+            if (lane == 0) page_pre = ex;
+        }
+        __syncthreads();
+        const uint4 pre = page_pre;
+        incl_all = add4(pre, tot);
+        uint4 carry = add4(add4(pre, woff), sub4(ti, run));
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t kk = 4 * tid + r;
+            if (kk < K) {
+                uint4 info = make_uint4(0, 0, kBad, 0);
+                const size_t blk = kBlocksPerPage * (size_t)p + kk;
+                if (!bad) {
+                    const uint4 m = __ldcg(reinterpret_cast<const uint4*>(pm + kk));
+                    const uint32_t a = area_s[kk];
+                    const uint32_t c = (m.w >> 8) & 0xFF ? (m.w >> 16) & 0xFF : 0u;
+                    info = make_uint4(m.x, (a & 0x3FFFu) | ((a & 0x8000u) ? kRaw : 0u) | ((a & 0x4000u) ? kDirect : 0u),
+                                      (m.w & 0xFF) | c << 8, 0);
+                    if (a & 0x4000u) {
+                        // a block of a pair decoded here: its differences
+                        // (in its own output) become its integers
+                        uint4* o = reinterpret_cast<uint4*>(out + 128 * blk);
+                        uint4 acc = carry;
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const uint4 f = o[rr];
+                            uint4 y;
+                            if (DELTA == ICX_DELTA_4) {
+                                acc = add4(acc, f);
+                                y = acc;
+                            } else {
+                                y.x = acc.x + f.x;
+                                y.y = y.x + f.y;
+                                y.z = y.y + f.z;
+                                y.w = y.z + f.w;
+                                acc.x = y.w;
+                            }
+                            o[rr] = y;
+                        }
+                    }
+                }
+                rec[2 * blk] = carry;
+                rec[2 * blk + 1] = info;
+            }
+            carry = add4(carry, v[r]);
+        }
+    }
+    // ---- the Variable Byte tail, after the last page
+    if (tail && warp == 0 && ((P > 0 && p == P - 1) || (P == 0 && p == 0))) {
+        uint4 carry = incl_all;
+        uint32_t* scratch = reinterpret_cast<uint32_t*>(S.start);
+        const uint64_t tstart = __ldg(index + P);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (tstart <= in_bytes && vbyte_decode_warp(in, tstart, in_bytes, tail, scratch, h))
+            v = *reinterpret_cast<const uint4*>(scratch + 4 * lane);
+        else if (tstart > in_bytes && lane == 0)
+            set_error(h, ICX_ECORRUPT);
+        __syncwarp();
+        uint4 o;
+        if (DELTA == ICX_DELTA_4) {
+            o = row_scan_d4(v, carry, lane);
+        } else {
+            v.y += v.x;
+            v.z += v.y;
+            v.w += v.z;
+            const uint32_t incl = warp_incl_scan(v.w, lane);
+            const uint32_t q = carry.x + incl - v.w;
+            o = make_uint4(v.x + q, v.y + q, v.z + q, v.w + q);
+        }
+        const size_t q0 = 128 * nb + 4 * (size_t)lane;
+        for (int c = 0; c < 4; ++c)
+            if (q0 + c < n) out[q0 + c] = comp(o, c);
+    }
+    finish_launch(h, epoch);
+}
+
+// ------------------------------------------------------------------ kernel 2
+
+namespace fp2 {
+
+// The records of pair p (loaded a step ahead): lane L's block record
+// (carry, then packed offset, area offset | raw, b | c << 8 | bad) and, in
+// lane 0, the page's offset in the stream.
+struct Pre {
+    uint4 carry, info;
+    uint64_t page;
+};
+
+// Pair p as the warp decodes it: its staged copy (space bytes) holds the
+// packed low bits (Sp bytes from the page offset `first`) and then the area
+// of its output region (`area` bytes); this lane's rows and entries are at
+// pk_at and ent_at in it.  A pair the prepare kernel decoded, or of a
+// corrupt page, is not ok.
+struct Desc {
+    uint64_t page;
+    uint32_t first, Sp, area, space, K;
+    uint32_t b, c, pk_at, ent_at;
+    bool ok;
+    uint4 carry;
+};
+
+// Entries (position | high << 8, in position order) of the lane's block: the
+// next one n and the one after it q sit in registers, so applying one never
+// waits for the load of the next; 0xFF marks the end.
+template <class Src>
+struct EntryHook {
+    Src src;
+    uint32_t n, q, at, end, b;
+    __device__ __forceinline__ uint32_t fetch() {
+        uint32_t v = 0xFFu;
+        if (at < end) {
+            v = src(at);
+            at += 4;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void operator()(uint4& f, int r) {
+        const uint32_t e = 4 * (uint32_t)r + 4;
+        while ((n & 0xFFu) < e) {
+            const uint32_t k = n & 3, v = (n >> 8) << b;
+            f.x |= k == 0 ? v : 0u;
+            f.y |= k == 1 ? v : 0u;
+            f.z |= k == 2 ? v : 0u;
+            f.w |= k == 3 ? v : 0u;
+            n = q;
+            q = fetch();
+        }
+    }
+};
+
+struct SmemWords {
+    uint32_t sb;
+    __device__ __forceinline__ uint32_t operator()(uint32_t off) const {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(sb + off) : "memory");
+        return v;
+    }
+};
+
+// Decodes and stores the lane's block of pair `pair_first / 4096`: the walk
+// from `carry` with the entries OR-ed into their fields.
+template <int DELTA, int STORE, class Rows, class Words, class Mid>
+__device__ __forceinline__ void stream_blocks(const Rows& rows, Words words, const Desc& d, uint32_t* __restrict__ out,
+                                              size_t pair_first, uint8_t* rest, int lane, Mid& mid) {
+    using namespace bl;
+    const bool live = (uint32_t)lane < d.K;
+    Walk w;
+    w.b = d.b;
+    w.mask = width_mask(d.b);
+    w.r0 = rows(d.pk_at);
+    w.r1 = rows(d.pk_at + 16);
+    w.nxt = rows.cursor(d.pk_at + 32);
+    w.sh = 0;
+    w.acc = d.carry;
+    w.prev = make_uint4(0, 0, 0, 0);
+    w.live = live;
+    w.dst = out + pair_first + 128 * (size_t)lane;
+    const uint32_t q = lane >> 3, i7 = lane & 7;
+    w.wsb = smem_u32(rest) + 128 * lane + 16 * (lane & 7);
+    const uint32_t rsb = smem_u32(rest) + 128 * q;
+    w.ro0 = rsb + 16 * (i7 ^ q);
+    w.ro1 = rsb + 16 * (i7 ^ (q + 4));
+    w.ob = out + pair_first + 128 * q + 4 * i7;
+    w.actq = __ballot_sync(FULL, w.live) >> q;
+    const uint32_t maxb = __reduce_max_sync(FULL, d.b);
+    EntryHook<Words> pt{words, 0xFFu, 0xFFu, d.ent_at, d.ent_at + 4 * d.c, d.b};
+    pt.n = pt.fetch();
+    pt.q = pt.fetch();
+    if (maxb <= 8)
+        walk_block<DELTA, true, STORE, 4>(rows, w, mid, pt);
+    else if (maxb <= 16)
+        walk_block<DELTA, true, STORE, 2>(rows, w, mid, pt);
+    else
+        walk_block<DELTA, true, STORE, 1>(rows, w, mid, pt);
+}
+
+}  // namespace fp2
+
+template <int DELTA, int STORE>
+__global__ void __maxnreg__(96)
+    fastpfor_stream_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
+                           const uint64_t* __restrict__ index, const uint4* __restrict__ rec, WsHeader* h) {
+    using namespace bl;
+    using fp2::Desc;
+    using fp2::Pre;
+    extern __shared__ __align__(128) uint8_t smem[];
+    Hdr& S = *reinterpret_cast<Hdr*>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t* ring = smem + kHdr + (size_t)warp * kWarpSmem;
+    uint8_t* rest = ring + kRing + kSlack;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(&S.bar[2 * warp]);
+    const size_t nb = n / 128;
+    const uint32_t P = (uint32_t)((nb + 31) / 32);
+    const uint32_t NW = gridDim.x * kW;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+    }
+    fence_mbar_init();
+    __syncwarp();
+
+    auto load = [&](uint32_t p) -> Pre {
+        Pre e;
+        const size_t blk = 32 * (size_t)p + lane;
+        e.carry = make_uint4(0, 0, 0, 0);
+        e.info = make_uint4(0, 0, fp2::kBad, 0);
+        if (p < P && blk < nb) {
+            e.carry = __ldcs(rec + 2 * blk);
+            e.info = __ldcs(rec + 2 * blk + 1);
+        }
+        e.page = lane == 0 && p < P ? __ldg(index + p / fp2::kPairsPerPage) : 0ull;
+        return e;
+    };
+    auto describe = [&](uint32_t p, const Pre& e) -> Desc {
+        Desc d;
+        d.page = __shfl_sync(FULL, e.page, 0);
+        d.K = (uint32_t)min((size_t)32, nb - 32 * (size_t)p);
+        const bool active = (uint32_t)lane < d.K;
+        d.ok = !__any_sync(FULL, active && ((e.info.z & fp2::kBad) || (e.info.y & fp2::kDirect))) && d.page < in_bytes;
+        const bool live = active && d.ok;
+        const bool raw = live && (e.info.y & fp2::kRaw);
+        const uint32_t b = live ? e.info.z & 0xFF : 0u;
+        d.c = live && !raw ? (e.info.z >> 8) & 0xFF : 0u;
+        const uint32_t ent = e.info.y & 0x3FFFu;
+        const uint32_t E = !live ? 0u : raw ? 128u : d.c;
+        d.first = __shfl_sync(FULL, e.info.x, 0);
+        const uint32_t last_end = __shfl_sync(FULL, e.info.x + 16 * b, (int)max(d.K, 1u) - 1);
+        d.Sp = d.ok ? last_end - d.first : 0u;
+        d.area = (4 * __reduce_add_sync(FULL, E) + 15) & ~15u;
+        d.space = d.ok ? d.Sp + d.area : 0u;
+        if (d.space > kRing) {  // the prepare kernel sends no such pair
+            if (lane == 0) set_error(h, ICX_ECORRUPT);
+            d.ok = false;
+            d.space = 0;
+        }
+        d.b = raw ? 32u : b;
+        d.pk_at = !live ? 0u : raw ? d.Sp + 4 * ent : e.info.x - d.first;
+        d.ent_at = live ? d.Sp + 4 * ent : 0u;
+        d.carry = e.carry;
+        return d;
+    };
+    // two-slot staging ring, as in the block-per-lane decoder
+    uint32_t s_iss = 0, s_wt = 0;
+    bool broken = false;
+    auto slot = [&](uint32_t s, const Desc& d) -> uint32_t { return (s & 1) ? kRing - d.space : 0u; };
+    const uint64_t drop = l2_policy_evict_first();
+    auto issue = [&](uint32_t p, const Desc& d) -> uint32_t {
+        const uint32_t s = s_iss;
+        if (!broken) {
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(bar + (s & 1), d.space);
+            }
+            if (d.space) {
+                __syncwarp();
+                uint8_t* dst = ring + slot(s, d);
+                if (lane == 0 && d.Sp) bulk_load_hint(dst, in + d.page + d.first, d.Sp, bar + (s & 1), drop);
+                if (lane == 1 && d.area) {
+                    fence_proxy_async();
+                    bulk_load_hint(dst + d.Sp, out + 4096 * (size_t)p, d.area, bar + (s & 1), drop);
+                }
+            }
+            ++s_iss;
+        }
+        return s;
+    };
+    auto wait = [&]() -> bool {
+        if (broken) return false;
+        const bool ok = __all_sync(FULL, mbar_wait(bar + (s_wt & 1), (s_wt >> 1) & 1u));
+        if (ok) {
+            ++s_wt;
+        } else {
+            broken = true;
+            if (lane == 0) set_error(h, ICX_ETIMEOUT);
+        }
+        return ok;
+    };
+    auto fits = [&](const Desc& a, const Desc& b) { return a.space + b.space <= kRing; };
+
+    uint32_t pc = blockIdx.x * kW + warp;
+    if (pc < P) {
+        Desc dc = describe(pc, load(pc));
+        uint32_t s_cur = issue(pc, dc);
+        uint32_t pn = pc + NW;
+        Pre en = load(pn);
+        while (pc < P) {
+            const uint32_t pk = pn + NW;
+            Pre ek{};
+            bool mid_done = false;
+            auto mid = [&]() {
+                ek = load(pk);
+                mid_done = true;
+            };
+            Desc dn;
+            uint32_t s_nx = 0;
+            bool nx_issued = false;
+            if (pn < P) {
+                dn = describe(pn, en);
+                if (fits(dc, dn)) {
+                    s_nx = issue(pn, dn);
+                    nx_issued = true;
+                }
+            }
+            if (wait() && dc.ok) {
+                uint8_t* base = ring + slot(s_cur, dc);
+                fp2::stream_blocks<DELTA, STORE>(SmemRows{base, smem_u32(base)}, fp2::SmemWords{smem_u32(base)}, dc,
+                                                 out, 4096 * (size_t)pc, rest, lane, mid);
+            }
+            __syncwarp();
+            if (!mid_done) mid();
+            if (pn < P && !nx_issued) s_nx = issue(pn, dn);
+            pc = pn;
+            pn = pk;
+            en = ek;
+            dc = dn;
+            s_cur = s_nx;
+        }
+    }
+    // a copy that never landed must not outlive the CTA's shared memory
+    if (broken)
+        for (uint32_t s = s_wt; s < s_iss; ++s) mbar_wait(bar + (s & 1), (s >> 1) & 1u);
+}
+
+// ------------------------------------------------------------------ launcher
+
+template <int DELTA, int STORE>
+static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
+                                BlockMeta* meta, uint32_t* pmeta, uint2* umeta, WsHeader* h, size_t ws_bytes,
+                                cudaStream_t s) {
+    auto prep = fastpfor_prep_kernel<DELTA>;
+    auto kern = fastpfor_stream_kernel<DELTA, STORE>;
+    const int smem = (int)(bl::kHdr + (size_t)bl::kW * bl::kWarpSmem);
+    static int blocks_per_sm = -1;
+    static int sms = 0;
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(prep, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, bl::kW * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, Q = (nb + 31) / 32;
+    uint4* rec = reinterpret_cast<uint4*>(blocklane_scratch(h, n, ws_bytes).bst);
+    prep<<<(unsigned)max(P, (size_t)1), kMetaThreads, 0, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, rec, h,
+                                                             (uint32_t)(n - 128 * nb));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || Q == 0) return e;
+    const BlocklaneTuning t = blocklane_tuning();
+    size_t G = max((size_t)1, min((size_t)blocks_per_sm * sms, (Q + bl::kW - 1) / bl::kW));
+    if (t.ctas > 0 && (size_t)t.ctas < G) G = (size_t)t.ctas;
+    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, rec, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fastpfor_two_kernel(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                       const uint64_t* index, BlockMeta* meta, uint32_t* pmeta, uint2* umeta,
+                                       WsHeader* h, size_t ws_bytes, cudaStream_t s) {
+    int st = blocklane_tuning().store;
+    if (st == bl::kStoreV8 && (reinterpret_cast<uintptr_t>(out) & 31u) != 0) st = bl::kStoreV4;
+#define ICX_FP2(D)                                                                                                  \
+    if (delta == D) {                                                                                               \
+        if (st == bl::kStoreRestage)                                                                                \
+            return launch_fp2_t<D, bl::kStoreRestage>(in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s); \
+        if (st == bl::kStoreV8)                                                                                     \
+            return launch_fp2_t<D, bl::kStoreV8>(in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);  \
+        return launch_fp2_t<D, bl::kStoreV4>(in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);      \
+    }
+    ICX_FP2(ICX_DELTA_4)
+    ICX_FP2(ICX_DELTA_1)
+#undef ICX_FP2
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace icx

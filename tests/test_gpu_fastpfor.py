@@ -60,6 +60,17 @@ def test_fastpfor_decode_matches_oracle(case, delta):
 def test_fastpfor_every_exception_width():
     # blocks of zeros with a few values of bit length d: b = 0, exceptions of
     # width d, counts 1, 127, 128, 129 per page (Sec. 5)
+    _every_exception_width(0)
+
+
+@pytest.mark.parametrize("delta", [icx.DELTA_1, icx.DELTA_4])
+def test_fastpfor_every_exception_width_with_deltas(delta):
+    # the same values as differences: high parts of every width 1..32 through
+    # entries (up to 24 bits) and through blocks decoded whole (wider)
+    _every_exception_width(delta)
+
+
+def _every_exception_width(delta):
     for d in range(1, 33):
         for total in (1, 127, 128, 129):
             nblocks = (total + 4) // 5
@@ -69,9 +80,10 @@ def test_fastpfor_every_exception_width():
                 for e in range(min(5, left)):
                     x[128 * k + 3 + 17 * e] = (1 << (d - 1)) | ((k * 7 + e) & ((1 << (d - 1)) - 1))
                 left -= min(5, left)
-            enc = oracle.fastpfor_encode(x, 0)
-            y, st = gpu_decode(enc, x.size, 0)
-            assert st == icx.OK and np.array_equal(y, x), (d, total)
+            xs = oracle.delta_decode(x, 4 if delta == icx.DELTA_4 else 1) if delta else x
+            enc = oracle.fastpfor_encode(xs, delta)
+            y, st = gpu_decode(enc, x.size, delta)
+            assert st == icx.OK and np.array_equal(y, xs), (d, total)
 
 
 def test_fastpfor_index_matches_oracle():
@@ -199,7 +211,7 @@ def test_fastpfor_positions_out_of_order(delta):
     assert st == icx.OK
     assert np.array_equal(y, want), int(np.argmax(y != want))
     # and the same stream through both decoders
-    for mode in (1, 0):
+    for mode in (2, 1, 0):
         icx.set_tuning("fastpfor.blocklane", mode)
         try:
             y0, st0 = gpu_decode(enc, n, delta)

@@ -67,8 +67,19 @@ def test_blocklane_variants_match_oracle(streams):
     few warps take all the tasks, group scans and the tail), the shortest and
     the longest lead of sums before decodes, and the single-pass decoders
     they replace."""
-    icx.set_tuning("fastpfor.blocklane", 1)
     try:
+        for fp_mode in (2, 1):  # the two SIMD-FastPFOR decoders that take these settings
+            icx.set_tuning("fastpfor.blocklane", fp_mode)
+            for store in (0, 1, 2):
+                icx.set_tuning("bp128.blocklane_store", store)
+                for ctas in (0, 1, 5):
+                    icx.set_tuning("bp128.blocklane_ctas", ctas)
+                    for codec, delta, fmt, enc, idx, want in streams:
+                        if codec == "fastpfor":
+                            assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), (fp_mode, store, ctas)
+            icx.set_tuning("bp128.blocklane_ctas", 0)
+            icx.set_tuning("bp128.blocklane_store", -1)
+        icx.set_tuning("fastpfor.blocklane", 1)
         for store in (0, 1, 2):
             icx.set_tuning("bp128.blocklane_store", store)
             for ctas in (0, 1, 2, 5):
