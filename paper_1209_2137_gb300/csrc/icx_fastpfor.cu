@@ -452,6 +452,22 @@ __global__ void __launch_bounds__(W * 32, 16 / W) simplepfor_decode_pipe_kernel(
 
 // ------------------------------------------------------------ launchers
 
+// The page parse of the SIMD layout alone (one CTA per page).
+cudaError_t launch_fastpfor_meta(const uint8_t* in, size_t in_bytes, size_t n, const uint64_t* index, BlockMeta* meta,
+                                 uint32_t* pmeta, uint2* umeta, WsHeader* h, cudaStream_t s) {
+    static bool carveout = false;
+    if (!carveout) {
+        // the page parse wants 7 CTAs of 30 KB per SM
+        const cudaError_t e = cudaFuncSetAttribute(fastpfor_meta_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                   cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        carveout = true;
+    }
+    const size_t P = (n / 128 + kBlocksPerPage - 1) / kBlocksPerPage;
+    if (P) fastpfor_meta_kernel<<<(unsigned)P, kMetaThreads, 0, s>>>(in, in_bytes, n, index, meta, pmeta, umeta, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fastpfor_index(const uint8_t* in, size_t in_bytes, size_t n, int fmt, uint64_t* index,
                                   WsHeader* h, cudaStream_t s) {
     fastpfor_index_kernel<<<1, 32, 0, s>>>(in, in_bytes, n, fmt, index, h);

@@ -80,210 +80,191 @@ struct NoMid {
 
 // ------------------------------------------------------------------ kernel 1
 
+namespace fp2 {
+constexpr int kPrepThreads = 256;  // blocks per tile of the prepare kernel (half a page)
+}
+
 template <int DELTA>
-__global__ void __launch_bounds__(kMetaThreads, 7)
+__global__ void __launch_bounds__(fp2::kPrepThreads, 4)
     fastpfor_prep_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
-                         const uint64_t* __restrict__ index, BlockMeta* __restrict__ meta,
-                         uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta, uint4* __restrict__ rec,
-                         WsHeader* h, uint32_t tail) {
+                         const uint64_t* __restrict__ index, const BlockMeta* __restrict__ meta,
+                         const uint32_t* __restrict__ pmeta, uint4* __restrict__ rec, uint4* __restrict__ tile_sum,
+                         WsHeader* h) {
     using namespace fp2;
     using namespace bl;
-    constexpr int NL = DELTA == ICX_DELTA_4 ? 4 : 1;
-    __shared__ MetaSmem S;
-    __shared__ uint4 wtot[kMetaThreads / 32];
-    __shared__ uint4 page_pre;
-    __shared__ uint32_t arr_s[32];
-    __shared__ uint32_t pid_s;
+    constexpr int NWARP = kPrepThreads / 32;
+    __shared__ uint4 wtot[NWARP];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t epoch = launch_epoch(h);
-    const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage;
-    if (tid == 0) pid_s = atomicAdd(&h->tile_counter, 1u);
-    __syncthreads();
-    const uint32_t p = pid_s;
-    uint4 incl_all = make_uint4(0, 0, 0, 0);  // inclusive prefix through this page
-    if (p < P) {
-        const uint32_t K = (uint32_t)min((size_t)kBlocksPerPage, nb - kBlocksPerPage * (size_t)p);
-        const uint64_t base = __ldg(index + p), end = __ldg(index + p + 1);
-        BlockMeta* pm = meta + kBlocksPerPage * (size_t)p;
-        uint32_t* pg = pmeta + kPageMetaWords * (size_t)p;
-        const bool bad = parse_page<ICX_FMT_PAPER>(S, in, in_bytes, base, end, K, pm, pg,
-                                                   umeta + kUnitsPerPage * (size_t)p, h);
-        if (tid < 32) arr_s[tid] = bad ? 0u : __ldcg(pg + tid);
-        __syncthreads();
-        // the jump tables are free now: block sums and area offsets
-        uint4* sums = reinterpret_cast<uint4*>(S.ja);
-        uint16_t* area_s = S.jb;
-        static_assert(sizeof(S.ja) >= kBlocksPerPage * sizeof(uint4), "block sums fit the jump table");
-        const uint8_t* page = in + base;
-        // ---- per block: its sum, its entries (or its differences)
-#pragma unroll 1
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t k = 128 * warp + 32 * i + lane;
-            const bool valid = !bad && k < K;
-            uint32_t b = 0, d = 0, c = 0, pk = 0, po = 0, cur = 0;
-            if (valid) {
-                const uint4 m = __ldcg(reinterpret_cast<const uint4*>(pm + k));
-                pk = m.x;
-                po = m.y;
-                cur = m.z;
-                b = m.w & 0xFF;
-                d = (m.w >> 8) & 0xFF;
-                c = d ? (m.w >> 16) & 0xFF : 0u;
-            }
-            // exceptions that an entry cannot hold make the block raw
-            bool raw = d > kHighMax, corrupt = false;
-            {
-                uint32_t prev = 0;
-                for (uint32_t j = 0; j < c; ++j) {
-                    const uint32_t q = __ldg(page + po + j);
-                    corrupt |= q >= 128;
-                    if (q >= 128 || (j && q <= prev)) raw = true;
-                    prev = q;
-                }
-            }
-            if (__any_sync(FULL, corrupt) && lane == 0) set_error(h, ICX_ECORRUPT);
-            // a pair whose packed bits and area do not fit the decoder's
-            // staging slot is decoded here, every block in its own output
-            uint32_t E = !valid ? 0u : raw ? 128u : c;
-            const uint32_t Sp = __reduce_add_sync(FULL, 16 * b);
-            const bool direct = Sp + ((4 * __reduce_add_sync(FULL, E) + 15) & ~15u) > kRing;
-            if (direct) E = 0;
-            const uint32_t eincl = warp_incl_scan(E, lane);
-            const uint32_t ent = eincl - E;
-            uint32_t* area = direct ? out + 128 * (kBlocksPerPage * (size_t)p + k)
-                                    : out + 4096 * ((size_t)kPairsPerPage * p + 4 * warp + i) + ent;
-            // the low parts' sum: the block's fields, walked like the decoder
-            Walk w;
-            w.b = b;
-            w.mask = width_mask(b);
-            const PredRows rows{page, in_bytes - base};
-            w.r0 = valid ? rows(pk) : make_uint4(0, 0, 0, 0);
-            w.r1 = valid ? rows(pk + 16) : make_uint4(0, 0, 0, 0);
-            w.nxt = pk + 32;
-            w.sh = 0;
-            w.acc = make_uint4(0, 0, 0, 0);
-            const uint32_t maxb = __reduce_max_sync(FULL, b);
-            NoPatch np;
-            NoMid nm;
-            if (maxb && __any_sync(FULL, valid && !raw && !direct)) {
-                const PredRows rr{valid ? page : in, valid ? in_bytes - base : 0};
-                if (maxb <= 8)
-                    walk_block<DELTA, false, 0, 4>(rr, w, nm, np);
-                else if (maxb <= 16)
-                    walk_block<DELTA, false, 0, 2>(rr, w, nm, np);
-                else
-                    walk_block<DELTA, false, 0, 1>(rr, w, nm, np);
-            }
-            uint4 s = w.acc;
-            const uint8_t* arr = page + arr_s[d ? d - 1 : 0];
-            if (valid && !raw && !direct) {
-                for (uint32_t j = 0; j < c; ++j) {
-                    const uint32_t q = __ldg(page + po + j);
-                    const uint32_t hv = high_part(arr, cur + j, d);
-                    area[j] = q | hv << 8;
-                    const uint32_t x = hv << b;
-                    s.x += (q & 3) == 0 ? x : 0u;
-                    s.y += (q & 3) == 1 ? x : 0u;
-                    s.z += (q & 3) == 2 ? x : 0u;
-                    s.w += (q & 3) == 3 ? x : 0u;
-                }
-            } else if (valid) {
-                // the 128 differences: low parts, then every exception OR-ed in
-                const uint32_t mask = width_mask(b);
-                for (uint32_t r = 0; r < 32; ++r) {
-                    const uint32_t bit = r * b, wo = 16 * (bit >> 5), sh = bit & 31;
-                    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-                    if (b) {
-                        lo = rows(pk + wo);
-                        if (sh + b > 32) hi = rows(pk + wo + 16);
-                    }
-                    *reinterpret_cast<uint4*>(area + 4 * r) =
-                        make_uint4(__funnelshift_r(lo.x, hi.x, sh) & mask, __funnelshift_r(lo.y, hi.y, sh) & mask,
-                                   __funnelshift_r(lo.z, hi.z, sh) & mask, __funnelshift_r(lo.w, hi.w, sh) & mask);
-                }
-                for (uint32_t j = 0; j < c; ++j) {
-                    const uint32_t q = __ldg(page + po + j);
-                    if (q < 128) area[q] |= high_part(arr, cur + j, d) << b;
-                }
-                s = make_uint4(0, 0, 0, 0);
-                for (uint32_t r = 0; r < 32; ++r) s = add4(s, *reinterpret_cast<const uint4*>(area + 4 * r));
-            }
-            if (k < K) {
-                sums[k] = DELTA == ICX_DELTA_4 ? s : make_uint4(s.x + s.y + s.z + s.w, 0, 0, 0);
-                area_s[k] = (uint16_t)(ent | (raw ? 0x8000u : 0u) | (direct ? 0x4000u : 0u));
-            }
+    const size_t nb = n / 128;
+    const uint32_t t = blockIdx.x;  // tile: blocks 256 t .. 256 t + 255
+    {
+        const size_t k = (size_t)kPrepThreads * t + tid;  // this thread's block
+        const size_t pgi = k / kBlocksPerPage;           // a tile lies in one page
+        const uint64_t base = __ldg(index + pgi);
+        const uint32_t* pg = pmeta + kPageMetaWords * pgi;
+        const bool bad = __ldg(pg + 32) != 0 || base >= in_bytes;
+        const bool valid = !bad && k < nb;
+        uint32_t b = 0, d = 0, c = 0, pk = 0, po = 0, cur = 0;
+        if (valid) {
+            const uint4 m = __ldg(reinterpret_cast<const uint4*>(meta + k));
+            pk = m.x;
+            po = m.y;
+            cur = m.z;
+            b = m.w & 0xFF;
+            d = (m.w >> 8) & 0xFF;
+            c = d ? (m.w >> 16) & 0xFF : 0u;
         }
-        __syncthreads();
-        // ---- the page's scan: thread t takes blocks 4t .. 4t+3
-        uint4 v[4], run = make_uint4(0, 0, 0, 0);
+        const uint8_t* page = in + (bad ? 0 : base);
+        const uint8_t* arr = page + (d ? __ldg(pg + d - 1) : 0u);
+        // positions, four at a time with their loads in flight together;
+        // exceptions that an entry cannot hold make the block raw
+        bool raw = d > kHighMax, corrupt = false;
+        {
+            uint32_t prev = 0;
+            for (uint32_t j0 = 0; j0 < c; j0 += 4) {
+                uint32_t q[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const uint32_t kk = 4 * tid + r;
-            v[r] = kk < K ? sums[kk] : make_uint4(0, 0, 0, 0);
-            run = add4(run, v[r]);
+                for (int i = 0; i < 4; ++i) q[i] = j0 + i < c ? __ldg(page + po + j0 + i) : 0u;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (j0 + i < c) {
+                        corrupt |= q[i] >= 128;
+                        if (q[i] >= 128 || (j0 + i && q[i] <= prev)) raw = true;
+                        prev = q[i];
+                    }
+                }
+            }
         }
-        const uint4 ti = warp_scan_carry<DELTA>(run, lane);
+        if (__any_sync(FULL, corrupt) && lane == 0) set_error(h, ICX_ECORRUPT);
+        // a pair (this warp's 32 blocks) whose packed bits and area do not
+        // fit the decoder's staging slot is decoded here, every block in its
+        // own output
+        uint32_t E = !valid ? 0u : raw ? 128u : c;
+        const uint32_t Sp = __reduce_add_sync(FULL, 16 * b);
+        const bool direct = Sp + ((4 * __reduce_add_sync(FULL, E) + 15) & ~15u) > kRing;
+        if (direct) E = 0;
+        const uint32_t ent = warp_incl_scan(E, lane) - E;
+        uint32_t* area = direct ? out + 128 * k : out + 4096 * (k / 32) + ent;
+        // the low parts' sum: the block's fields, walked like the decoder
+        Walk w;
+        w.b = b;
+        w.mask = width_mask(b);
+        const PredRows rows{page, bad ? 0 : in_bytes - base};
+        w.r0 = valid ? rows(pk) : make_uint4(0, 0, 0, 0);
+        w.r1 = valid ? rows(pk + 16) : make_uint4(0, 0, 0, 0);
+        w.nxt = pk + 32;
+        w.sh = 0;
+        w.acc = make_uint4(0, 0, 0, 0);
+        const uint32_t maxb = __reduce_max_sync(FULL, valid && !raw && !direct ? b : 0u);
+        NoPatch np;
+        NoMid nm;
+        if (maxb) {
+            if (maxb <= 8)
+                walk_block<DELTA, false, 0, 4>(rows, w, nm, np);
+            else if (maxb <= 16)
+                walk_block<DELTA, false, 0, 2>(rows, w, nm, np);
+            else
+                walk_block<DELTA, false, 0, 1>(rows, w, nm, np);
+        }
+        uint4 s = w.acc;
+        if (valid && !raw && !direct) {
+            for (uint32_t j0 = 0; j0 < c; j0 += 4) {
+                uint32_t q[4], hv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool in_range = j0 + i < c;
+                    q[i] = in_range ? __ldg(page + po + j0 + i) : 0u;
+                    hv[i] = in_range ? high_part(arr, cur + j0 + i, d) : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (j0 + i < c) {
+                        area[j0 + i] = q[i] | hv[i] << 8;
+                        const uint32_t x = hv[i] << b;
+                        s.x += (q[i] & 3) == 0 ? x : 0u;
+                        s.y += (q[i] & 3) == 1 ? x : 0u;
+                        s.z += (q[i] & 3) == 2 ? x : 0u;
+                        s.w += (q[i] & 3) == 3 ? x : 0u;
+                    }
+                }
+            }
+        } else if (valid) {
+            // the 128 differences: low parts, then every exception OR-ed in
+            const uint32_t mask = width_mask(b);
+            for (uint32_t r = 0; r < 32; ++r) {
+                const uint32_t bit = r * b, wo = 16 * (bit >> 5), sh = bit & 31;
+                uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                if (b) {
+                    lo = rows(pk + wo);
+                    if (sh + b > 32) hi = rows(pk + wo + 16);
+                }
+                *reinterpret_cast<uint4*>(area + 4 * r) =
+                    make_uint4(__funnelshift_r(lo.x, hi.x, sh) & mask, __funnelshift_r(lo.y, hi.y, sh) & mask,
+                               __funnelshift_r(lo.z, hi.z, sh) & mask, __funnelshift_r(lo.w, hi.w, sh) & mask);
+            }
+            for (uint32_t j = 0; j < c; ++j) {
+                const uint32_t q = __ldg(page + po + j);
+                if (q < 128) area[q] |= high_part(arr, cur + j, d) << b;
+            }
+            s = make_uint4(0, 0, 0, 0);
+            for (uint32_t r = 0; r < 32; ++r) s = add4(s, *reinterpret_cast<const uint4*>(area + 4 * r));
+        }
+        if (DELTA == ICX_DELTA_1) s = make_uint4(s.x + s.y + s.z + s.w, 0, 0, 0);
+        // ---- the tile's scan: each block's carry within the tile, and the
+        // tile's total (the scan over tiles adds the tiles before it)
+        const uint4 ti = warp_scan_carry<DELTA>(s, lane);
         if (lane == 31) wtot[warp] = ti;
         __syncthreads();
         uint4 woff = make_uint4(0, 0, 0, 0), tot = woff;
 #pragma unroll
-        for (int ww = 0; ww < kMetaThreads / 32; ++ww) {
+        for (int ww = 0; ww < NWARP; ++ww) {
             if (ww < warp) woff = add4(woff, wtot[ww]);
             tot = add4(tot, wtot[ww]);
         }
-        if (warp == 0) {
-            const uint4 ex = lookback<NL>(h, epoch, p, tot);
-            if (lane == 0) page_pre = ex;
-        }
-        __syncthreads();
-        const uint4 pre = page_pre;
-        incl_all = add4(pre, tot);
-        uint4 carry = add4(add4(pre, woff), sub4(ti, run));
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const uint32_t kk = 4 * tid + r;
-            if (kk < K) {
-                uint4 info = make_uint4(0, 0, kBad, 0);
-                const size_t blk = kBlocksPerPage * (size_t)p + kk;
-                if (!bad) {
-                    const uint4 m = __ldcg(reinterpret_cast<const uint4*>(pm + kk));
-                    const uint32_t a = area_s[kk];
-                    const uint32_t c = (m.w >> 8) & 0xFF ? (m.w >> 16) & 0xFF : 0u;
-                    info = make_uint4(m.x, (a & 0x3FFFu) | ((a & 0x8000u) ? kRaw : 0u) | ((a & 0x4000u) ? kDirect : 0u),
-                                      (m.w & 0xFF) | c << 8, 0);
-                    if (a & 0x4000u) {
-                        // a block of a pair decoded here: its differences
-                        // (in its own output) become its integers
-                        uint4* o = reinterpret_cast<uint4*>(out + 128 * blk);
-                        uint4 acc = carry;
-                        for (int rr = 0; rr < 32; ++rr) {
-                            const uint4 f = o[rr];
-                            uint4 y;
-                            if (DELTA == ICX_DELTA_4) {
-                                acc = add4(acc, f);
-                                y = acc;
-                            } else {
-                                y.x = acc.x + f.x;
-                                y.y = y.x + f.y;
-                                y.z = y.y + f.z;
-                                y.w = y.z + f.w;
-                                acc.x = y.w;
-                            }
-                            o[rr] = y;
-                        }
-                    }
-                }
-                rec[2 * blk] = carry;
-                rec[2 * blk + 1] = info;
-            }
-            carry = add4(carry, v[r]);
+        if (tid == 0) tile_sum[t] = tot;
+        if (k < nb) {
+            uint4 info = make_uint4(0, 0, kBad, 0);
+            if (!bad) info = make_uint4(pk, ent | (raw ? kRaw : 0u) | (direct ? kDirect : 0u), b | c << 8, 0);
+            rec[2 * k] = add4(woff, sub4(ti, s));
+            rec[2 * k + 1] = info;
         }
     }
-    // ---- the Variable Byte tail, after the last page
-    if (tail && warp == 0 && ((P > 0 && p == P - 1) || (P == 0 && p == 0))) {
-        uint4 carry = incl_all;
-        uint32_t* scratch = reinterpret_cast<uint32_t*>(S.start);
-        const uint64_t tstart = __ldg(index + P);
+}
+
+// The scan over tiles (one CTA): each tile's exclusive prefix replaces its
+// total; warp 0 then decodes the Variable Byte tail (Sec. 2.4) with the sum
+// of every block as its carry.
+constexpr int kScanThreads = 1024;
+
+template <int DELTA>
+__global__ void __launch_bounds__(kScanThreads)
+    fastpfor_tile_scan_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
+                              const uint64_t* __restrict__ index, uint4* __restrict__ tile_sum, WsHeader* h,
+                              uint32_t tail) {
+    __shared__ uint4 wtot[kScanThreads / 32];
+    __shared__ __align__(16) uint32_t scratch[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t nb = n / 128, T = (nb + fp2::kPrepThreads - 1) / fp2::kPrepThreads;
+    const size_t per = (T + kScanThreads - 1) / kScanThreads, t0 = per * tid, t1 = min(T, t0 + per);
+    uint4 run = make_uint4(0, 0, 0, 0);
+    for (size_t t = t0; t < t1; ++t) run = add4(run, tile_sum[t]);
+    const uint4 ti = bl::warp_scan_carry<DELTA>(run, lane);
+    if (lane == 31) wtot[warp] = ti;
+    __syncthreads();
+    uint4 off = make_uint4(0, 0, 0, 0), total = off;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < warp) off = add4(off, wtot[w]);
+        total = add4(total, wtot[w]);
+    }
+    uint4 acc = add4(off, sub4(ti, run));
+    for (size_t t = t0; t < t1; ++t) {
+        const uint4 v = tile_sum[t];
+        tile_sum[t] = acc;
+        acc = add4(acc, v);
+    }
+    if (tail && warp == 0) {
+        uint4 carry = total;
+        const uint64_t tstart = __ldg(index + (nb + kBlocksPerPage - 1) / kBlocksPerPage);
         uint4 v = make_uint4(0, 0, 0, 0);
         if (tstart <= in_bytes && vbyte_decode_warp(in, tstart, in_bytes, tail, scratch, h))
             v = *reinterpret_cast<const uint4*>(scratch + 4 * lane);
@@ -302,10 +283,9 @@ __global__ void __launch_bounds__(kMetaThreads, 7)
             o = make_uint4(v.x + q, v.y + q, v.z + q, v.w + q);
         }
         const size_t q0 = 128 * nb + 4 * (size_t)lane;
-        for (int c = 0; c < 4; ++c)
-            if (q0 + c < n) out[q0 + c] = comp(o, c);
+        for (int cc = 0; cc < 4; ++cc)
+            if (q0 + cc < n) out[q0 + cc] = comp(o, cc);
     }
-    finish_launch(h, epoch);
 }
 
 // ------------------------------------------------------------------ kernel 2
@@ -317,19 +297,20 @@ namespace fp2 {
 // lane 0, the page's offset in the stream.
 struct Pre {
     uint4 carry, info;
+    uint32_t tpre;  // lane j < 4: component j of the tile's prefix
     uint64_t page;
 };
 
 // Pair p as the warp decodes it: its staged copy (space bytes) holds the
 // packed low bits (Sp bytes from the page offset `first`) and then the area
 // of its output region (`area` bytes); this lane's rows and entries are at
-// pk_at and ent_at in it.  A pair the prepare kernel decoded, or of a
-// corrupt page, is not ok.
+// pk_at and ent_at in it.  A pair of a corrupt page is not ok; a pair the
+// prepare kernel left as differences in its output is `direct`.
 struct Desc {
     uint64_t page;
     uint32_t first, Sp, area, space, K;
     uint32_t b, c, pk_at, ent_at;
-    bool ok;
+    bool ok, direct;
     uint4 carry;
 };
 
@@ -413,7 +394,8 @@ __device__ __forceinline__ void stream_blocks(const Rows& rows, Words words, con
 template <int DELTA, int STORE>
 __global__ void __maxnreg__(96)
     fastpfor_stream_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
-                           const uint64_t* __restrict__ index, const uint4* __restrict__ rec, WsHeader* h) {
+                           const uint64_t* __restrict__ index, const uint4* __restrict__ rec,
+                           const uint4* __restrict__ tile_pre, WsHeader* h) {
     using namespace bl;
     using fp2::Desc;
     using fp2::Pre;
@@ -442,6 +424,9 @@ __global__ void __maxnreg__(96)
             e.carry = __ldcs(rec + 2 * blk);
             e.info = __ldcs(rec + 2 * blk + 1);
         }
+        e.tpre = p < P && lane < 4
+                     ? __ldg(reinterpret_cast<const uint32_t*>(tile_pre + (32 * (size_t)p) / fp2::kPrepThreads) + lane)
+                     : 0u;
         e.page = lane == 0 && p < P ? __ldg(index + p / fp2::kPairsPerPage) : 0ull;
         return e;
     };
@@ -450,7 +435,9 @@ __global__ void __maxnreg__(96)
         d.page = __shfl_sync(FULL, e.page, 0);
         d.K = (uint32_t)min((size_t)32, nb - 32 * (size_t)p);
         const bool active = (uint32_t)lane < d.K;
-        d.ok = !__any_sync(FULL, active && ((e.info.z & fp2::kBad) || (e.info.y & fp2::kDirect))) && d.page < in_bytes;
+        const bool good = !__any_sync(FULL, active && (e.info.z & fp2::kBad)) && d.page < in_bytes;
+        d.direct = good && __any_sync(FULL, active && (e.info.y & fp2::kDirect));
+        d.ok = good && !d.direct;
         const bool live = active && d.ok;
         const bool raw = live && (e.info.y & fp2::kRaw);
         const uint32_t b = live ? e.info.z & 0xFF : 0u;
@@ -470,7 +457,9 @@ __global__ void __maxnreg__(96)
         d.b = raw ? 32u : b;
         d.pk_at = !live ? 0u : raw ? d.Sp + 4 * ent : e.info.x - d.first;
         d.ent_at = live ? d.Sp + 4 * ent : 0u;
-        d.carry = e.carry;
+        const uint4 tp = make_uint4(__shfl_sync(FULL, e.tpre, 0), __shfl_sync(FULL, e.tpre, 1),
+                                    __shfl_sync(FULL, e.tpre, 2), __shfl_sync(FULL, e.tpre, 3));
+        d.carry = add4(e.carry, tp);
         return d;
     };
     // two-slot staging ring, as in the block-per-lane decoder
@@ -539,6 +528,26 @@ __global__ void __maxnreg__(96)
                 uint8_t* base = ring + slot(s_cur, dc);
                 fp2::stream_blocks<DELTA, STORE>(SmemRows{base, smem_u32(base)}, fp2::SmemWords{smem_u32(base)}, dc,
                                                  out, 4096 * (size_t)pc, rest, lane, mid);
+            } else if (dc.direct && (uint32_t)lane < dc.K) {
+                // the block's differences (in its own output) become its
+                // integers
+                uint4* o = reinterpret_cast<uint4*>(out + 4096 * (size_t)pc + 128 * lane);
+                uint4 acc = dc.carry;
+                for (int r = 0; r < 32; ++r) {
+                    const uint4 f = __ldcg(o + r);
+                    uint4 y;
+                    if (DELTA == ICX_DELTA_4) {
+                        acc = add4(acc, f);
+                        y = acc;
+                    } else {
+                        y.x = acc.x + f.x;
+                        y.y = y.x + f.y;
+                        y.z = y.y + f.z;
+                        y.w = y.z + f.w;
+                        acc.x = y.w;
+                    }
+                    __stcs(o + r, y);
+                }
             }
             __syncwarp();
             if (!mid_done) mid();
@@ -569,8 +578,6 @@ static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* ou
     if (blocks_per_sm < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(prep, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -579,15 +586,23 @@ static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* ou
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, Q = (nb + 31) / 32;
-    uint4* rec = reinterpret_cast<uint4*>(blocklane_scratch(h, n, ws_bytes).bst);
-    prep<<<(unsigned)max(P, (size_t)1), kMetaThreads, 0, s>>>(in, in_bytes, out, n, index, meta, pmeta, umeta, rec, h,
-                                                             (uint32_t)(n - 128 * nb));
+    const size_t T = (nb + fp2::kPrepThreads - 1) / fp2::kPrepThreads;
+    const bl::Scratch sc = blocklane_scratch(h, n, ws_bytes);
+    uint4* rec = reinterpret_cast<uint4*>(sc.bst);        // 32 bytes per block
+    uint4* tiles = reinterpret_cast<uint4*>(sc.ptot);     // 16 bytes per tile (8 pairs)
+    if (P > 0) {
+        const cudaError_t em = launch_fastpfor_meta(in, in_bytes, n, index, meta, pmeta, umeta, h, s);
+        if (em != cudaSuccess) return em;
+        prep<<<(unsigned)T, fp2::kPrepThreads, 0, s>>>(in, in_bytes, out, n, index, meta, pmeta, rec, tiles, h);
+    }
+    fastpfor_tile_scan_kernel<DELTA><<<1, kScanThreads, 0, s>>>(in, in_bytes, out, n, index, tiles, h,
+                                                                 (uint32_t)(n - 128 * nb));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || Q == 0) return e;
     const BlocklaneTuning t = blocklane_tuning();
     size_t G = max((size_t)1, min((size_t)blocks_per_sm * sms, (Q + bl::kW - 1) / bl::kW));
     if (t.ctas > 0 && (size_t)t.ctas < G) G = (size_t)t.ctas;
-    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, rec, h);
+    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, rec, tiles, h);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ cudaError_t launch_fastpfor_decode(int delta, int fmt, const uint8_t* in, size_t
 cudaError_t launch_fastpfor_blocklane(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                       const uint64_t* index, const BlockMeta* meta, const uint32_t* pmeta,
                                       const uint2* umeta, WsHeader* h, size_t ws_bytes, cudaStream_t s);
+cudaError_t launch_fastpfor_meta(const uint8_t* in, size_t in_bytes, size_t n, const uint64_t* index, BlockMeta* meta,
+                                 uint32_t* pmeta, uint2* umeta, WsHeader* h, cudaStream_t s);
 cudaError_t launch_fastpfor_two_kernel(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
                                        const uint64_t* index, BlockMeta* meta, uint32_t* pmeta, uint2* umeta,
                                        WsHeader* h, size_t ws_bytes, cudaStream_t s);
