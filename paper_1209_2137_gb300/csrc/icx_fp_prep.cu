@@ -82,6 +82,7 @@ struct NoMid {
 
 namespace fp2 {
 constexpr int kPrepThreads = 256;  // blocks per tile of the prepare kernel (half a page)
+constexpr uint32_t kCoopMax = 2048;  // exceptions of a pair handled by the whole warp
 }
 
 template <int DELTA>
@@ -94,6 +95,12 @@ __global__ void __launch_bounds__(fp2::kPrepThreads, 4)
     using namespace bl;
     constexpr int NWARP = kPrepThreads / 32;
     __shared__ uint4 wtot[NWARP];
+    // per warp: the owner lane of each of the pair's exceptions, each lane's
+    // exception parameters, area offset and exception sums
+    __shared__ uint8_t own_s[NWARP][kCoopMax];
+    __shared__ uint4 par_s[NWARP][32];
+    __shared__ uint4 xsum_s[NWARP][32];
+    __shared__ uint32_t ent_s[NWARP][32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t nb = n / 128;
     const uint32_t t = blockIdx.x;  // tile: blocks 256 t .. 256 t + 255
@@ -116,10 +123,44 @@ __global__ void __launch_bounds__(fp2::kPrepThreads, 4)
         }
         const uint8_t* page = in + (bad ? 0 : base);
         const uint8_t* arr = page + (d ? __ldg(pg + d - 1) : 0u);
-        // positions, four at a time with their loads in flight together;
-        // exceptions that an entry cannot hold make the block raw
+        // The pair's exceptions (block after block) are taken by the whole
+        // warp, 32 at a time, when there are at most kCoopMax of them (each
+        // lane finds its exception's block in own_s); otherwise each lane
+        // takes its own block's.  First pass: positions strictly increasing
+        // inside each block and below 128, else the block is raw (as is a
+        // block whose high parts are wider than an entry holds).
+        const uint32_t cincl = warp_incl_scan(c, lane), ctot = __shfl_sync(FULL, cincl, 31);
+        const uint32_t cex = cincl - c;
+        const bool coop = ctot <= kCoopMax;
         bool raw = d > kHighMax, corrupt = false;
-        {
+        if (coop) {
+            for (uint32_t j = 0; j < c; ++j) own_s[warp][cex + j] = (uint8_t)lane;
+            par_s[warp][lane] = make_uint4(po, cur, d ? __ldg(pg + d - 1) : 0u, b | d << 8 | cex << 16);
+            xsum_s[warp][lane] = make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            uint32_t marked = 0, carry_p = 0, carry_o = 0xFFu;
+            for (uint32_t q0 = 0; q0 < ctot; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const bool v = q < ctot;
+                const uint32_t o = v ? own_s[warp][q] : 0xFFu;
+                uint32_t pos = 0;
+                if (v) {
+                    const uint4 pr = par_s[warp][o];
+                    pos = __ldg(page + pr.x + (q - (pr.w >> 16)));
+                }
+                uint32_t pp = __shfl_up_sync(FULL, pos, 1), po_ = __shfl_up_sync(FULL, o, 1);
+                if (lane == 0) {
+                    pp = carry_p;
+                    po_ = carry_o;
+                }
+                carry_p = __shfl_sync(FULL, pos, 31);
+                carry_o = __shfl_sync(FULL, o, 31);
+                const bool out_of_order = v && (pos >= 128 || (po_ == o && pos <= pp));
+                corrupt |= v && pos >= 128;
+                marked |= __reduce_or_sync(FULL, out_of_order ? 1u << o : 0u);
+            }
+            raw |= (marked >> lane) & 1u;
+        } else {
             uint32_t prev = 0;
             for (uint32_t j0 = 0; j0 < c; j0 += 4) {
                 uint32_t q[4];
@@ -167,7 +208,30 @@ __global__ void __launch_bounds__(fp2::kPrepThreads, 4)
                 walk_block<DELTA, false, 0, 1>(rows, w, nm, np);
         }
         uint4 s = w.acc;
-        if (valid && !raw && !direct) {
+        if (coop && !direct) {
+            // second pass: the entries of the blocks that are not raw, and
+            // the exceptions' share of each block sum
+            ent_s[warp][lane] = ent;
+            const unsigned rawmask = __ballot_sync(FULL, raw);
+            __syncwarp();
+            uint32_t* region = out + 4096 * (k / 32);
+            for (uint32_t q0 = 0; q0 < ctot; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                if (q < ctot) {
+                    const uint32_t o = own_s[warp][q];
+                    if (!((rawmask >> o) & 1u)) {
+                        const uint4 pr = par_s[warp][o];
+                        const uint32_t j = q - (pr.w >> 16), od = (pr.w >> 8) & 0xFF, ob = pr.w & 0xFF;
+                        const uint32_t pos = __ldg(page + pr.x + j);
+                        const uint32_t hv = high_part(page + pr.z, pr.y + j, od);
+                        region[ent_s[warp][o] + j] = pos | hv << 8;
+                        atomicAdd(reinterpret_cast<uint32_t*>(&xsum_s[warp][o]) + (pos & 3), hv << ob);
+                    }
+                }
+            }
+            __syncwarp();
+            if (valid && !raw) s = add4(s, xsum_s[warp][lane]);
+        } else if (valid && !raw && !direct) {
             for (uint32_t j0 = 0; j0 < c; j0 += 4) {
                 uint32_t q[4], hv[4];
 #pragma unroll
@@ -188,7 +252,8 @@ __global__ void __launch_bounds__(fp2::kPrepThreads, 4)
                     }
                 }
             }
-        } else if (valid) {
+        }
+        if (valid && (raw || direct)) {
             // the 128 differences: low parts, then every exception OR-ed in
             const uint32_t mask = width_mask(b);
             for (uint32_t r = 0; r < 32; ++r) {
