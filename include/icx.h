@@ -274,6 +274,8 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *       a kernel that parses, sums and prepares every block and one that
  *       streams the integers out; 1: one block-per-lane kernel after the page
  *       parse; 0: the tile decoder with a chained look-back (-1 = default);
+ *   "fastpfor.stream_warps" = 4, 5 or 6 warps per CTA of the SIMD-FastPFOR
+ *       stream kernel (0 = default: 4 for stride 1, 6 for stride 4);
  *   "bp128.blocklane_store" = 0 (default: through shared memory, coalesced
  *       16-byte stores), 1 (32-byte stores per lane), 2 (16-byte stores per
  *       lane): output path of the two-pass decoders;

@@ -244,6 +244,10 @@ icx_status icx_set_tuning(const char* key, int value) {
         icx::set_bp128_blocklane(value);
         return ICX_OK;
     }
+    if (!strcmp(key, "fastpfor.stream_warps")) {
+        icx::set_fastpfor_stream_warps(value);
+        return ICX_OK;
+    }
     if (!strcmp(key, "fastpfor.blocklane")) {
         icx::set_fastpfor_blocklane(value);
         return ICX_OK;

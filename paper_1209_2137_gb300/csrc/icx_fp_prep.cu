@@ -456,8 +456,10 @@ __device__ __forceinline__ void stream_blocks(const Rows& rows, Words words, con
 
 }  // namespace fp2
 
-template <int DELTA, int STORE>
-__global__ void __maxnreg__(96)
+// W warps per CTA: 6 (three CTAs of 96 registers a thread per SM) or 4 / 5
+// (128 registers a thread).
+template <int DELTA, int STORE, int W>
+__global__ void __maxnreg__(W == 6 ? 96 : 128)
     fastpfor_stream_kernel(const uint8_t* __restrict__ in, size_t in_bytes, uint32_t* __restrict__ out, size_t n,
                            const uint64_t* __restrict__ index, const uint4* __restrict__ rec,
                            const uint4* __restrict__ tile_pre, WsHeader* h) {
@@ -472,7 +474,8 @@ __global__ void __maxnreg__(96)
     uint64_t* bar = reinterpret_cast<uint64_t*>(&S.bar[2 * warp]);
     const size_t nb = n / 128;
     const uint32_t P = (uint32_t)((nb + 31) / 32);
-    const uint32_t NW = gridDim.x * kW;
+    static_assert(W >= 1 && W <= kW, "the header holds barriers for kW warps");
+    const uint32_t NW = gridDim.x * W;
     if (lane == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
@@ -565,7 +568,7 @@ __global__ void __maxnreg__(96)
     };
     auto fits = [&](const Desc& a, const Desc& b) { return a.space + b.space <= kRing; };
 
-    uint32_t pc = blockIdx.x * kW + warp;
+    uint32_t pc = blockIdx.x * W + warp;
     if (pc < P) {
         Desc dc = describe(pc, load(pc));
         uint32_t s_cur = issue(pc, dc);
@@ -631,13 +634,16 @@ __global__ void __maxnreg__(96)
 
 // ------------------------------------------------------------------ launcher
 
-template <int DELTA, int STORE>
-static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
-                                BlockMeta* meta, uint32_t* pmeta, uint2* umeta, WsHeader* h, size_t ws_bytes,
-                                cudaStream_t s) {
-    auto prep = fastpfor_prep_kernel<DELTA>;
-    auto kern = fastpfor_stream_kernel<DELTA, STORE>;
-    const int smem = (int)(bl::kHdr + (size_t)bl::kW * bl::kWarpSmem);
+static int g_fp_stream_warps = 0;  // warps per CTA of the stream kernel (0: by stride)
+
+void set_fastpfor_stream_warps(int w) { g_fp_stream_warps = (w >= 4 && w <= 6) ? w : 0; }
+
+template <int DELTA, int STORE, int W>
+static cudaError_t launch_stream_w(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,
+                                   const uint64_t* index, const uint4* rec, const uint4* tiles, WsHeader* h,
+                                   cudaStream_t s) {
+    auto kern = fastpfor_stream_kernel<DELTA, STORE, W>;
+    const int smem = (int)(bl::kHdr + (size_t)W * bl::kWarpSmem);
     static int blocks_per_sm = -1;
     static int sms = 0;
     if (blocks_per_sm < 0) {
@@ -646,10 +652,22 @@ static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* ou
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, bl::kW * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, W * 32, smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
+    const size_t Q = (n / 128 + 31) / 32;
+    const BlocklaneTuning t = blocklane_tuning();
+    size_t G = max((size_t)1, min((size_t)blocks_per_sm * sms, (Q + W - 1) / W));
+    if (t.ctas > 0 && (size_t)t.ctas < G) G = (size_t)t.ctas;
+    kern<<<(int)G, W * 32, smem, s>>>(in, in_bytes, out, n, index, rec, tiles, h);
+    return cudaGetLastError();
+}
+
+template <int DELTA, int STORE>
+static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n, const uint64_t* index,
+                                BlockMeta* meta, uint32_t* pmeta, uint2* umeta, WsHeader* h, size_t ws_bytes,
+                                cudaStream_t s) {
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, Q = (nb + 31) / 32;
     const size_t T = (nb + fp2::kPrepThreads - 1) / fp2::kPrepThreads;
     const bl::Scratch sc = blocklane_scratch(h, n, ws_bytes);
@@ -658,17 +676,23 @@ static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* ou
     if (P > 0) {
         const cudaError_t em = launch_fastpfor_meta(in, in_bytes, n, index, meta, pmeta, umeta, h, s);
         if (em != cudaSuccess) return em;
-        prep<<<(unsigned)T, fp2::kPrepThreads, 0, s>>>(in, in_bytes, out, n, index, meta, pmeta, rec, tiles, h);
+        fastpfor_prep_kernel<DELTA><<<(unsigned)T, fp2::kPrepThreads, 0, s>>>(in, in_bytes, out, n, index, meta,
+                                                                              pmeta, rec, tiles, h);
     }
     fastpfor_tile_scan_kernel<DELTA><<<1, kScanThreads, 0, s>>>(in, in_bytes, out, n, index, tiles, h,
                                                                  (uint32_t)(n - 128 * nb));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || Q == 0) return e;
-    const BlocklaneTuning t = blocklane_tuning();
-    size_t G = max((size_t)1, min((size_t)blocks_per_sm * sms, (Q + bl::kW - 1) / bl::kW));
-    if (t.ctas > 0 && (size_t)t.ctas < G) G = (size_t)t.ctas;
-    kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, rec, tiles, h);
-    return cudaGetLastError();
+    // measured on the 2^26 sorted arrays: stride 1 is fastest with 4 warps a
+    // CTA (0.1254 vs 0.1295 ms with 6), stride 4 with 6 (0.1418 vs 0.1510)
+    const int w = g_fp_stream_warps ? g_fp_stream_warps : (DELTA == ICX_DELTA_1 ? 4 : 6);
+    if constexpr (STORE == bl::kStoreRestage) {
+        if (w == 4)
+            return launch_stream_w<DELTA, STORE, 4>(in, in_bytes, out, n, index, rec, tiles, h, s);
+        if (w == 5)
+            return launch_stream_w<DELTA, STORE, 5>(in, in_bytes, out, n, index, rec, tiles, h, s);
+    }
+    return launch_stream_w<DELTA, STORE, 6>(in, in_bytes, out, n, index, rec, tiles, h, s);
 }
 
 cudaError_t launch_fastpfor_two_kernel(int delta, const uint8_t* in, size_t in_bytes, uint32_t* out, size_t n,

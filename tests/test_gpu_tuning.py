@@ -68,6 +68,12 @@ def test_blocklane_variants_match_oracle(streams):
     the longest lead of sums before decodes, and the single-pass decoders
     they replace."""
     try:
+        for w in (4, 5, 6):  # warps per CTA of the SIMD-FastPFOR stream kernel
+            icx.set_tuning("fastpfor.stream_warps", w)
+            for codec, delta, fmt, enc, idx, want in streams:
+                if codec == "fastpfor":
+                    assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("stream warps", w, delta)
+        icx.set_tuning("fastpfor.stream_warps", 0)
         for fp_mode in (2, 1):  # the two SIMD-FastPFOR decoders that take these settings
             icx.set_tuning("fastpfor.blocklane", fp_mode)
             for store in (0, 1, 2):
@@ -114,6 +120,7 @@ def test_blocklane_variants_match_oracle(streams):
         icx.set_tuning("bp128.blocklane_sum_warps", 0)
         icx.set_tuning("bp128.blocklane", 1)
         icx.set_tuning("fastpfor.blocklane", -1)
+        icx.set_tuning("fastpfor.stream_warps", 0)
         icx.set_tuning("bp128.blocklane_store", -1)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane_lead", 0)
