@@ -17,6 +17,7 @@ scalar CPU oracle on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -46,7 +47,9 @@ COMBOS = [
 def kernel_name(codec: str, delta: int, fmt: int = 0) -> str:
     if codec == "bp128":
         return "bp128_blocklane_kernel" if fmt == 0 and delta else "bp128_decode_kernel"
-    return "fastpfor_decode_pipe_kernel" if delta == 4 else "fastpfor_decode_kernel"
+    if delta:  # one decode call launches four kernels
+        return "fastpfor_meta_kernel + fastpfor_prep_kernel + fastpfor_tile_scan_kernel + fastpfor_stream_kernel"
+    return "fastpfor_decode_kernel"
 
 
 def log(*a):
@@ -296,7 +299,8 @@ def run_gpu(args, world, rank, local):
     total_ms = max_over_ranks(float(step_ms.sum()), world)
     ints_per_step = sum(s["n"] for s in streams)
     value = aggregate_rate(ints_per_step * K, total_ms, world)
-    launches_per_step = sum(1 if s["codec"] == "bp128" else 2 for s in streams)
+    # SIMD-BP128: one kernel; SIMD-FastPFOR with a stride: page parse, prepare, tile scan and stream
+    launches_per_step = sum(1 if s["codec"] == "bp128" else 4 if s["delta"] else 2 for s in streams)
     ws.raise_status("timed decodes")
 
     # roofline per stream and for the dominant one
@@ -324,6 +328,7 @@ def run_gpu(args, world, rank, local):
     exceptions = None if args.skip_exceptions else run_exceptions(args, out, ws, flush_l2, world)
     intersect = None if args.skip_intersect else run_intersect(args, streams, arrays, out, ws, flush_l2, world)
     bp32 = None if args.skip_bp32 else run_bp32(args, arrays, out, ws, flush_l2, world)
+    encode = None if args.skip_encode else run_encode(args, arrays, dev, flush_l2, world)
     batched = serving = None
     if not args.skip_batch:
         del out
@@ -350,6 +355,7 @@ def run_gpu(args, world, rank, local):
         "exceptions": exceptions,
         "intersect": intersect,
         "bp32": bp32,
+        "encode": encode,
         "batched": batched,
         "serving": serving,
         "gpu_launches": launches_per_step * K,
@@ -429,6 +435,9 @@ def run_exceptions(args, out, ws, flush_l2, world):
 
     x = W.workload_exceptions()
     xt = torch.from_numpy(x).to(out.device)
+    if out.numel() < x.size or ws.n < x.size:  # a reduced main workload: buffers of this size
+        out = torch.empty(x.size, dtype=torch.uint32, device=out.device)
+        ws = icx.Workspace(x.size, device=out.device)
     o = out[: x.size]
     peak, _ = peaks()
     res = {"workload": f"{x.size} unsorted uint32: 90 % geometric (mean 8), 10 % uniform in [2^20, 2^28)"}
@@ -456,6 +465,81 @@ def run_exceptions(args, out, ws, flush_l2, world):
                       "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
     res["note"] = "the GPU encoders write the oracle's bytes (tests), so bits_per_int is the oracle's"
     log(f"[bench] exception-heavy: SIMD-FastPFOR {res['SIMD-FastPFOR']}, SIMD-BP128 {res['SIMD-BP128']}")
+    return res
+
+
+# ---------------------------------------------------------------- encode --
+
+ENCODE_COMBOS = [("bp128", 1, 0, "SIMD-BP128"), ("bp128", 4, 0, "SIMD-BP128*"),
+                 ("fastpfor", 1, 0, "SIMD-FastPFOR"), ("fastpfor", 4, 0, "SIMD-FastPFOR*")]
+
+
+def run_encode(args, arrays, dev, flush_l2, world):
+    """Coding speed (the paper reports it beside decoding speed, Sec. 6.4 and
+    6.5): the GPU encoders on the long sorted arrays, inputs resident, events
+    around each call; roofline bytes = 4 B per integer read + the stream and
+    index written.  Beside them, the oracle's encoder (one host thread) on a
+    2^22-integer prefix."""
+    import torch
+
+    import oracle
+    import paper_1209_2137_gb300 as icx
+
+    peak, _ = peaks()
+    L = icx.lib()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    res = {"workload": "the long sorted arrays of the main step, encoded on the GPU (bytes identical to the "
+                       "oracle's, tests)", "streams": []}
+    for name, x in arrays.items():
+        xt = torch.from_numpy(x).to(dev)
+        n = x.size
+        for codec, delta, fmt, label in ENCODE_COMBOS:
+            if codec == "bp128":
+                cap, ilen = icx.bp128_max_bytes(n, fmt), icx.bp128_index_len(n)
+            else:
+                cap, ilen = icx.fastpfor_max_bytes(n), icx.fastpfor_index_len(n)
+            buf = torch.empty(cap, dtype=torch.uint8, device=dev)
+            index = torch.empty(ilen, dtype=torch.uint64, device=dev)
+            total = torch.zeros(1, dtype=torch.uint64, device=dev)
+            ews = icx.Workspace(n, device=dev, encode=True)
+            fn = L.bp128_encode if codec == "bp128" else L.fastpfor_encode
+
+            def call():
+                code = fn(icx._ptr(xt), n, delta, fmt, icx._ptr(buf), cap, icx._ptr(index), icx._ptr(total),
+                          ews.ptr(), ews.bytes, sp)
+                if code != 0:
+                    raise SystemExit(f"{label} encode failed ({code})")
+
+            for _ in range(args.warmup):
+                flush_l2()
+                call()
+            torch.cuda.synchronize()
+            ews.raise_status(f"{label} encode")
+            steps = max(3, min(args.steps, 20))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush_l2()
+                a.record(stream)
+                call()
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world)
+            nbytes = int(total.cpu().view(torch.int64).item())
+            alg = 4 * n + nbytes + 8 * ilen
+            xs = x[: 1 << 22]
+            t = time.perf_counter()
+            oracle.encode(codec, xs, delta, fmt)
+            cpu_s = time.perf_counter() - t
+            res["streams"].append({"array": name, "codec": label, "n": int(n), "bits_per_int": round(8.0 * nbytes / n, 3),
+                                   "ms": round(ms, 4), "gints_s": round(n / (ms / 1e3) / 1e9, 1),
+                                   "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1),
+                                   "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4),
+                                   "oracle_gints_s": round(xs.size / cpu_s / 1e9, 4)})
+            del buf, index, total, ews
+        del xt
+        torch.cuda.empty_cache()
+    log("[bench] encode: " + ", ".join(f"{r['array']} {r['codec']} {r['ms']} ms ({r['frac']})" for r in res["streams"]))
     return res
 
 
@@ -732,54 +816,86 @@ def oracle_streams(arrays, prefix):
 
 
 def cpu_baseline(arrays, args):
-    """The oracle decoder as it stands (single thread) on a bounded sample."""
+    """The oracle decoder as it stands on a bounded sample: on every host core
+    (unit ranges on threads, plus the differential carry per range) and, for
+    comparison, on one thread."""
+    import concurrent.futures as cf
+
     import oracle
+    from oracle import parallel
     prefix = args.cpu_prefix
     enc = oracle_streams(arrays, prefix)
+    idx = [oracle.index(codec, data, n, fmt) for codec, delta, fmt, label, data, n in enc]
     t = time.perf_counter()
     ints = 0
     for codec, delta, fmt, label, data, n in enc:
         oracle.decode(codec, data, n, delta, fmt)
         ints += n
-    dt = time.perf_counter() - t
-    return {"value": round(ints / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {prefix} integers of each array, all 12 decodes ({ints} ints, {dt:.1f} s)"}
+    dt1 = time.perf_counter() - t
+    cores = parallel.host_cores()
+    with cf.ThreadPoolExecutor(max_workers=cores) as pool:
+        for (codec, delta, fmt, label, data, n), ix in zip(enc[:1], idx[:1]):  # warm the pool
+            parallel.decode_parallel(codec, data, n, delta, fmt, threads=cores, pool=pool, idx=ix)
+        t = time.perf_counter()
+        for (codec, delta, fmt, label, data, n), ix in zip(enc, idx):
+            parallel.decode_parallel(codec, data, n, delta, fmt, threads=cores, pool=pool, idx=ix)
+        dtn = time.perf_counter() - t
+    sample = f"first {prefix} integers of each array, all 12 decodes ({ints} ints)"
+    return {"value": round(ints / dtn / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample + f", {dtn:.2f} s on {cores} threads (unit ranges, carry added per range)",
+            "single_thread": {"value": round(ints / dt1 / 1e9, 4), "cores": 1, "seconds": round(dt1, 2)}}
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the scalar CPU oracle, each step a bounded sample."""
+    """Reference arm: the CPU oracle on every host core, each step a bounded
+    sample."""
     if rank != 0:
         return
+    import concurrent.futures as cf
+
     import oracle
+    from oracle import parallel
     arrays = workload_arrays(args.n)
+    cores = parallel.host_cores()
+    pool = cf.ThreadPoolExecutor(max_workers=cores)
+
+    def run(enc, idx):
+        for (codec, delta, fmt, label, data, n), ix in zip(enc, idx):
+            parallel.decode_parallel(codec, data, n, delta, fmt, threads=cores, pool=pool, idx=ix)
+
+    def indexed(enc):
+        return [oracle.index(codec, data, n, fmt) for codec, delta, fmt, label, data, n in enc]
+
     # size the per-step sample so the whole run stays within ~2 minutes
-    calib = oracle_streams({k: v[: 1 << 16] for k, v in arrays.items()}, 1 << 16)
+    calib = oracle_streams({k: v[: 1 << 20] for k, v in arrays.items()}, 1 << 20)
+    cidx = indexed(calib)
+    run(calib, cidx)
     t = time.perf_counter()
-    for codec, delta, fmt, label, data, n in calib:
-        oracle.decode(codec, data, n, delta, fmt)
+    run(calib, cidx)
     rate = sum(c[-1] for c in calib) / (time.perf_counter() - t)
     budget = 100.0 / max(1, args.steps + args.warmup)
-    prefix = int(min(1 << 26, max(2048, rate * budget / len(calib)))) // 2048 * 2048
+    prefix = int(min(1 << 26, max(65536, rate * budget / len(calib)))) // 65536 * 65536
     enc = oracle_streams(arrays, prefix)
+    idx = indexed(enc)
     for _ in range(args.warmup):
-        for codec, delta, fmt, label, data, n in enc:
-            oracle.decode(codec, data, n, delta, fmt)
+        run(enc, idx)
     t = time.perf_counter()
     for _ in range(args.steps):
-        for codec, delta, fmt, label, data, n in enc:
-            oracle.decode(codec, data, n, delta, fmt)
+        run(enc, idx)
     dt = time.perf_counter() - t
+    pool.shutdown()
     ints = sum(e[-1] for e in enc) * args.steps
     value = ints / dt / 1e9
-    sample = f"first {prefix} integers of each array per step, all 12 decodes"
+    sample = (f"first {prefix} integers of each array per step, all 12 decodes, on {cores} threads "
+              "(unit ranges, carry added per range)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64)",
         "config": {"workload": workload_label(arrays, [{"label": c[3]} for c in COMBOS for _ in arrays]),
-                   "parallelism": "single CPU thread", "sample_per_step": sample},
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "parallelism": f"{cores} CPU threads", "sample_per_step": sample},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -794,6 +910,7 @@ def main():
     ap.add_argument("--cpu-prefix", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fastpfor", action="store_true")
+    ap.add_argument("--skip-encode", action="store_true")
     ap.add_argument("--extra-none", action="store_true", help="also time decodes without differential decoding")
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")

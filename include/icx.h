@@ -129,6 +129,16 @@ icx_status icx_workspace_init(void *d_workspace, size_t workspace_bytes, icx_str
  * clears it.  Returns ICX_ECUDA if the copy fails, else ICX_OK. */
 icx_status icx_status_read(void *d_workspace, icx_stream_t stream, icx_status *out);
 
+/* Sets how long a decode's device waits on values other CTAs publish (block
+ * sums, look-back states) may see no progress before they give up with
+ * ICX_ETIMEOUT, in microseconds; 0 restores the default (2 s).  Kept in the
+ * workspace header (icx_workspace_init clears it), so it applies to later
+ * launches on that workspace only.  A test aid for the timeout path: a wait
+ * that runs out ends the kernel normally, with the status set.  ICX_EINVAL
+ * for a null or too small workspace. */
+icx_status icx_workspace_set_wait_limit(void *d_workspace, size_t workspace_bytes, unsigned usec,
+                                        icx_stream_t stream);
+
 /* ------------------------------------------------------------- index ---- */
 
 /* Walks the metablocks of a SIMD-BP128 (fmt = PAPER), W32 or BP32 stream and

@@ -64,6 +64,7 @@ def lib():
                 "icx_encode_workspace_bytes": ([sz], sz),
                 "icx_workspace_init": ([vp, sz, vp], i),
                 "icx_status_read": ([vp, vp, ctypes.POINTER(ctypes.c_int)], i),
+                "icx_workspace_set_wait_limit": ([vp, sz, ctypes.c_uint, vp], i),
                 "bp128_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
                 "fastpfor_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
                 "bp128_decode": ([vp, sz, vp, sz, i, i, vp, vp, sz, vp], i),
@@ -96,6 +97,7 @@ def lib():
 
 EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_bytes", "icx_fastpfor_max_bytes",
             "icx_workspace_bytes", "icx_encode_workspace_bytes", "icx_workspace_init", "icx_status_read",
+            "icx_workspace_set_wait_limit",
             "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "bp128_intersect",
             "sorted_intersect", "delta_decode", "delta_encode",
             "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning", "icx_plan_create",
@@ -173,6 +175,11 @@ class Workspace:
 
     def ptr(self):
         return _ptr(self.tensor)
+
+    def set_wait_limit(self, usec: int, stream=None):
+        """Limit of the decoders' device waits on this workspace (0 = default)."""
+        _check(lib().icx_workspace_set_wait_limit(self.ptr(), self.bytes, int(usec), _stream(stream)),
+               "icx_workspace_set_wait_limit")
 
     def status(self, stream=None) -> int:
         """Synchronises the stream, returns and clears the status word."""

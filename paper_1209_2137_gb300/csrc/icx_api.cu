@@ -61,6 +61,15 @@ icx_status icx_workspace_init(void* d_ws, size_t ws_bytes, icx_stream_t stream) 
     return from_cuda(cudaMemsetAsync(d_ws, 0, ws_bytes, (cudaStream_t)stream));
 }
 
+icx_status icx_workspace_set_wait_limit(void* d_ws, size_t ws_bytes, unsigned usec, icx_stream_t stream) {
+    if (!d_ws || ws_bytes < icx::kWsHeaderBytes) return ICX_EINVAL;
+    // from pageable memory: the value is staged before the call returns
+    const unsigned v = usec;
+    WsHeader* h = static_cast<WsHeader*>(d_ws);
+    return from_cuda(cudaMemcpyAsync(&h->aux[icx::kAuxWaitLimit], &v, sizeof(unsigned), cudaMemcpyHostToDevice,
+                                     (cudaStream_t)stream));
+}
+
 icx_status icx_status_read(void* d_ws, icx_stream_t stream, icx_status* out) {
     if (!d_ws || !out) return ICX_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

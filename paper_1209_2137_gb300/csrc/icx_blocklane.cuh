@@ -85,7 +85,7 @@ __device__ __forceinline__ uint4 wait_tagged(const unsigned long long* p, uint32
     if (ld_tagged<NL, IGN>(p, tag, v, t0)) return v;
     const unsigned long long ts = globaltimer();
     while (!ld_tagged<NL, IGN>(p, tag, v, t0)) {
-        if (globaltimer() - ts > kWaitLimitNs) {
+        if (globaltimer() - ts > wait_limit_ns(h)) {
             set_error(h, ICX_ETIMEOUT);
             break;
         }
@@ -564,7 +564,7 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
                 if (lane == 0) {
                     const unsigned long long t0 = globaltimer();
                     while (ld_acquire_u32(&h->aux[3]) != epoch + 1u) {
-                        if (globaltimer() - t0 > kWaitLimitNs) {
+                        if (globaltimer() - t0 > wait_limit_ns(h)) {
                             set_error(h, ICX_ETIMEOUT);
                             break;
                         }

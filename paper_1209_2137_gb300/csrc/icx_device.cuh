@@ -69,6 +69,10 @@ __host__ __device__ inline size_t ws_total_bytes(size_t n) { return ws_unitmeta_
 // A device wait that sees no progress for this long gives up with ETIMEOUT.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// Header word holding a shorter limit for the waits on published values (in
+// microseconds; 0 = kWaitLimitNs), set by icx_workspace_set_wait_limit.
+constexpr int kAuxWaitLimit = 5;
+
 __device__ __forceinline__ unsigned long long* tile_states(WsHeader* h) {
     return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h) + kWsHeaderBytes);
 }
@@ -87,6 +91,12 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// The limit of a wait on values other CTAs publish in this workspace.
+__device__ __forceinline__ unsigned long long wait_limit_ns(WsHeader* h) {
+    const unsigned v = *reinterpret_cast<volatile const unsigned*>(&h->aux[kAuxWaitLimit]);
+    return v ? 1000ull * v : kWaitLimitNs;
 }
 
 __device__ __forceinline__ void set_error(WsHeader* h, unsigned code) {
@@ -288,7 +298,7 @@ __device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsig
 // predecessors: lane i reads the state of tile end-1-i-32r with one or two
 // 128-bit loads.  Contributions are summed per lane and reduced once at the
 // end.  Returns the exclusive prefixes (components 0..NL-1) and publishes the
-// inclusive ones.  Every wait is bounded: after kWaitLimitNs without progress
+// inclusive ones.  Every wait is bounded: after wait_limit_ns without progress
 // the status word gets ICX_ETIMEOUT and the tile publishes what it has, so no
 // other tile can wait forever on it.
 // Publishes a tile's aggregate (the first tile publishes it as its inclusive
@@ -363,7 +373,7 @@ __device__ uint4 lookback_resolve_at(unsigned long long* st, WsHeader* h, uint32
         }
         if (wait) {
             if (t0 == 0) t0 = globaltimer();
-            if (globaltimer() - t0 > kWaitLimitNs) {
+            if (globaltimer() - t0 > wait_limit_ns(h)) {
                 if (lane == 0) set_error(h, ICX_ETIMEOUT);
                 break;
             }

@@ -89,13 +89,14 @@ __device__ __forceinline__ uint64_t array_bytes(uint32_t d, uint32_t nd) {
 
 // Whole warp: the exception arrays after a page's byte array.  Their offsets
 // follow from the page's per-width counts (lane d-1 holds cnt_total of
-// width d): after the bitset, each present width d has its stored count
-// (the first right after the bitset, the others 16-byte aligned) and then,
-// from the next 16-byte boundary, its array; so array d starts at the first
-// array's offset plus (16 + size) of every present width below d, one warp
-// scan.  Lane d-1 checks the stored count of array d against its total, and
-// the arrays must end exactly at the page end.  Writes the page record pg
-// (array offsets, then the flag word) and returns the warp-uniform `bad`.
+// width d): after the bitset, each present width d has its stored count and
+// then, from the next 16-byte boundary, its array of s_d bytes; the next
+// count follows the array directly.  So array starts advance by
+// pad16(s_d + 4) from the first (one warp scan), and a count sits s bytes
+// past the previous present width's array (the first right after the
+// bitset).  Lane d-1 checks the stored count of array d against its total,
+// and the arrays must end exactly at the page end.  Writes the page record
+// pg (array offsets, then the flag word) and returns the warp-uniform `bad`.
 template <int LAYOUT>
 __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize, uint32_t bytes_at, uint32_t Lpad,
                                             uint32_t cnt_total, bool bad, uint32_t* __restrict__ pg, WsHeader* h,
@@ -106,13 +107,19 @@ __device__ __forceinline__ bool page_arrays(const uint8_t* page, uint32_t psize,
         const uint32_t bitset = ld32(page + bytes_at + Lpad);
         present = (bitset >> lane) & 1u;
         if (!present && cnt_total) bad = true;
-        const uint32_t sz = present ? 16u + (uint32_t)array_bytes<LAYOUT>(lane + 1, cnt_total) : 0u;
-        const uint32_t incl = warp_incl_scan(sz, lane), total = __shfl_sync(FULL, incl, 31);
-        const uint32_t q0 = bytes_at + Lpad + 4;  // the first stored count
-        const uint32_t p0 = (uint32_t)pad_up(q0 + 4, 16);  // the first array
-        my_off = p0 + incl - sz;
-        my_cnt_at = incl == sz ? q0 : my_off - 16;
-        const uint64_t q_end = total ? (uint64_t)p0 + total - 16 : (uint64_t)q0;
+        const uint32_t sz = present ? (uint32_t)array_bytes<LAYOUT>(lane + 1, cnt_total) : 0u;
+        const uint32_t step = present ? (uint32_t)pad_up(sz + 4, 16) : 0u;
+        const uint32_t incl = warp_incl_scan(step, lane);
+        const uint32_t q0 = bytes_at + Lpad + 4;           // the first stored count
+        const uint32_t a0 = (uint32_t)pad_up(q0 + 4, 16);  // the first array
+        my_off = a0 + incl - step;
+        // the present width before this lane's: its array's end is this count
+        const unsigned below = __ballot_sync(FULL, present) & ((1u << lane) - 1u);
+        const int prev = below ? 31 - __clz(below) : 0;
+        const uint32_t prev_end = __shfl_sync(FULL, my_off + sz, prev);
+        my_cnt_at = below ? prev_end : q0;
+        const unsigned all = __ballot_sync(FULL, present);
+        const uint64_t q_end = all ? (uint64_t)__shfl_sync(FULL, my_off + sz, 31 - __clz(all)) : (uint64_t)q0;
         if (q_end > psize || pad_up(q_end, 16) != psize) bad = true;
     }
     bad = __any_sync(FULL, bad);
