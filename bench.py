@@ -380,12 +380,15 @@ def workload_label(arrays, streams):
 def run_e2e(args, streams, out, ws, dev, world):
     """Same metric through the public API with host buffers: every step copies
     each stream and its index from pinned host memory, decodes, and copies the
-    integers back to pinned host memory."""
+    integers back to pinned host memory.  The decodes of a step rotate over
+    `--e2e-streams` CUDA streams (each with its own buffers and workspace), so
+    one decode's copies overlap another's kernels on the two copy engines."""
     import torch
 
     import paper_1209_2137_gb300 as icx
 
     steps = max(3, min(args.steps, args.e2e_steps))
+    lanes = max(1, args.e2e_streams)
     host = []
     for s in streams:
         hd = torch.empty(s["enc"].nbytes, dtype=torch.uint8, pin_memory=True)
@@ -395,31 +398,49 @@ def run_e2e(args, streams, out, ws, dev, world):
         dd = torch.empty_like(s["enc"].data)
         di = torch.empty_like(s["enc"].index)
         host.append((hd, hi, dd, di))
-    hout = torch.empty(out.numel(), dtype=torch.uint32, pin_memory=True)
+    nmax = out.numel()
+    cuda = [torch.cuda.Stream(device=dev) for _ in range(lanes)]
+    outs = [out] + [torch.empty(nmax, dtype=torch.uint32, device=dev) for _ in range(lanes - 1)]
+    wss = [ws] + [icx.Workspace(nmax, device=dev) for _ in range(lanes - 1)]
+    houts = [torch.empty(nmax, dtype=torch.uint32, pin_memory=True) for _ in range(lanes)]
     h2d = sum(h[0].numel() + 8 * h[1].numel() for h in host)
     d2h = sum(4 * s["n"] for s in streams)
+    main = torch.cuda.current_stream()
 
     def step():
-        for s, (hd, hi, dd, di) in zip(streams, host):
-            dd.copy_(hd, non_blocking=True)
-            di.copy_(hi, non_blocking=True)
-            enc = icx.Encoded(dd, di, s["n"], s["codec"], s["delta"], s["fmt"])
-            icx.decode(enc, out=out[: s["n"]], workspace=ws)
-            hout[: s["n"]].copy_(out[: s["n"]], non_blocking=True)
+        start = torch.cuda.Event()
+        start.record(main)
+        for i, (s, (hd, hi, dd, di)) in enumerate(zip(streams, host)):
+            k = i % lanes
+            cs, o, w, ho = cuda[k], outs[k][: s["n"]], wss[k], houts[k][: s["n"]]
+            cs.wait_event(start)
+            with torch.cuda.stream(cs):
+                dd.copy_(hd, non_blocking=True)
+                di.copy_(hi, non_blocking=True)
+                enc = icx.Encoded(dd, di, s["n"], s["codec"], s["delta"], s["fmt"])
+                icx.decode(enc, out=o, workspace=w, stream=cs)
+                ho.copy_(o, non_blocking=True)
+        for cs in cuda:
+            main.wait_stream(cs)
 
     step()
     torch.cuda.synchronize()
+    for k in range(lanes):
+        wss[k].raise_status("e2e decode", cuda[k])
     barrier(world)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
+    a.record(main)
     for _ in range(steps):
         step()
-    b.record()
+    b.record(main)
     torch.cuda.synchronize()
     ms = max_over_ranks(a.elapsed_time(b), world)
+    for k in range(lanes):
+        wss[k].raise_status("e2e decode", cuda[k])
     ints = sum(s["n"] for s in streams) * steps * world
     return {"value": round(ints / (ms / 1e3) / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps}
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "cuda_streams": lanes,
+            "host_link_gbs": round((h2d + d2h) * steps * world / (ms / 1e3) / 1e9, 1)}
 
 
 # ------------------------------------------------- exception-heavy data --
@@ -773,8 +794,8 @@ def run_serving(args, pool, L):
     w = np.arange(1, len(L) + 1, dtype=np.float64) ** -1.1
     cum = np.cumsum(w) / w.sum()
     rows = []
-    for i, rate in enumerate(args.serve_rates):
-        nreq = int(rate * args.serve_seconds)
+    for i, rate in enumerate(list(args.serve_rates) + [0]):
+        nreq = int(rate * args.serve_seconds) if rate > 0 else args.serve_saturation
         z = W.splitmix64(W.SEED_BASE + 5, 100 * i, 3 * nreq)
         u = ((z[:nreq] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
         arrival = np.cumsum(-np.log(u) / rate * 1e9).astype(np.uint64)
@@ -784,10 +805,17 @@ def run_serving(args, pool, L):
         zz = W.splitmix64(W.SEED_BASE + 6, 100 * i, int(offs[-1]))
         uu = ((zz >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
         ids = by_rank[np.minimum(np.searchsorted(cum, uu), len(L) - 1)].astype(np.uint32)
+        if rate <= 0:  # closed loop at saturation: every request waiting at the start
+            arrival = np.zeros(nreq, dtype=np.uint64)
         lat, st, _ = sv.run(arrival, offs, ids)
         ms = lat.astype(np.float64) / 1e6
         span = float(arrival[-1]) / 1e9 if nreq else 0.0
-        rows.append({"rate_req_s": rate, "requests": nreq, "seconds": round(span, 2),
+        nb = max(1, int(st["batches"]))
+        rows.append({"rate_req_s": rate if rate > 0 else "saturation", "requests": nreq, "seconds": round(span, 2),
+                     "gpu_busy": round(st["gpu_s"] / max(st["wall_s"], 1e-9), 3),
+                     "mean_queue_ms": round(1e3 * st["queue_s"] / max(1, nreq), 4),
+                     "mean_batch_service_ms": round(1e3 * st["service_s"] / nb, 4),
+                     "mean_batch_gpu_ms": round(1e3 * st["gpu_s"] / nb, 4),
                      "p50_ms": round(float(np.percentile(ms, 50)), 3), "p99_ms": round(float(np.percentile(ms, 99)), 3),
                      "max_ms": round(float(ms.max()), 3),
                      "gints_s": round(st["ints"] / max(st["wall_s"], 1e-9) / 1e9, 3),
@@ -800,6 +828,8 @@ def run_serving(args, pool, L):
     return {"workload": "the batch's pool resident in HBM; Poisson arrivals; k ~ U{2..8} lists per request, "
                         "weight rank^-1.1 by length; FCFS admission", "budget_bytes": args.serve_budget,
             "streams": args.serve_streams, "latency": "scheduled arrival -> completion event observed (host)",
+            "breakdown": "a request's latency = queue (arrival to its batch's issue) + batch service (issue to "
+                         "completion seen by the host) = queue + batch GPU time (copies + kernel) + host loop",
             "rates": rows}
 
 
@@ -911,6 +941,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fastpfor", action="store_true")
     ap.add_argument("--skip-encode", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=3, help="CUDA streams the end-to-end decodes rotate over")
     ap.add_argument("--extra-none", action="store_true", help="also time decodes without differential decoding")
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
     ap.add_argument("--bp128-warps", type=int, default=0, help="warps per CTA of the SIMD-BP128 decoder")
@@ -926,8 +957,10 @@ def main():
     ap.add_argument("--batch-total", type=int, default=1 << 28)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--skip-serve", action="store_true", help="skip the serving loop")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 10000, 100000])
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10000, 100000, 300000, 1000000])
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-saturation", type=int, default=300000,
+                    help="requests of the closed-loop run (all waiting at the start)")
     ap.add_argument("--serve-budget", type=int, default=16 << 30)
     ap.add_argument("--serve-streams", type=int, default=2)
     args = ap.parse_args()

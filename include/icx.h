@@ -407,6 +407,9 @@ typedef struct {
     uint64_t max_queue;       /* most requests waiting for admission */
     uint64_t peak_bytes;      /* most decode-buffer bytes in use */
     double wall_s;            /* first arrival to last completion */
+    double queue_s;           /* summed over requests: arrival to its batch's issue */
+    double service_s;         /* summed over batches: issue to completion seen by the host */
+    double gpu_s;             /* summed over batches: GPU time, first copy to last kernel */
 } icx_server_stats;
 
 /* Creates a server over `pool` (d_out ignored; every other field as for a

@@ -545,7 +545,8 @@ class ListPool:
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("ints", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("max_batch", ctypes.c_uint64), ("max_queue", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("wall_s", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("service_s", ctypes.c_double),
+                ("gpu_s", ctypes.c_double)]
 
 
 class Server:

@@ -1106,7 +1106,9 @@ struct icx_server {
     Arena alloc;
     struct Lane {
         cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev = nullptr;   // the batch's work done
+        cudaEvent_t ev0 = nullptr;  // before its copies (GPU time of the batch: ev0 -> ev)
+        uint64_t t_launch = 0;      // host time the batch was issued
         icx::WsHeader* ws = nullptr;
         icx::ServeItem* d_items = nullptr;
         icx::InstDev* d_insts = nullptr;
@@ -1130,6 +1132,7 @@ void icx_server_destroy(icx_server* sv) {
             cudaStreamDestroy(l.st);
         }
         if (l.ev) cudaEventDestroy(l.ev);
+        if (l.ev0) cudaEventDestroy(l.ev0);
         if (l.h_items) cudaFreeHost(l.h_items);
         if (l.h_insts) cudaFreeHost(l.h_insts);
     }
@@ -1270,7 +1273,7 @@ icx_status icx_server_create(const icx_list_desc* pool, size_t nlists, size_t bu
         l.d_items = reinterpret_cast<ServeItem*>(b + ws_bytes);
         l.d_insts = reinterpret_cast<InstDev*>(b + ws_bytes + pad256(sizeof(ServeItem) * kServeMaxItems));
         if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&l.ev) != cudaSuccess || cudaEventCreate(&l.ev0) != cudaSuccess ||
             cudaMallocHost(&l.h_items, sizeof(ServeItem) * kServeMaxItems) != cudaSuccess ||
             cudaMallocHost(&l.h_insts, sizeof(InstDev) * kServeMaxInsts) != cudaSuccess)
             return fail(ICX_ECUDA);
@@ -1328,6 +1331,9 @@ icx_status icx_server_run(icx_server* sv, size_t nreq, const uint64_t* arrival_n
     icx_status err = ICX_OK;
     auto complete = [&](icx_server::Lane& l) {
         const uint64_t t = now_ns();
+        float gpu_ms = 0.f;
+        if (cudaEventElapsedTime(&gpu_ms, l.ev0, l.ev) == cudaSuccess) S.gpu_s += 1e-3 * gpu_ms;
+        S.service_s += 1e-9 * (double)(t - l.t_launch);
         for (size_t q = 0; q < l.reqs.size(); ++q) {
             const uint32_t r = l.reqs[q];
             latency_ns[r] = t - arrival_ns[r];
@@ -1381,6 +1387,9 @@ icx_status icx_server_run(icx_server* sv, size_t nreq, const uint64_t* arrival_n
         if (l.reqs.empty()) return false;
         S.batches++;
         S.max_batch = std::max<uint64_t>(S.max_batch, l.reqs.size());
+        l.t_launch = now_ns();
+        for (const uint32_t r : l.reqs) S.queue_s += 1e-9 * (double)(l.t_launch - std::min(l.t_launch, arrival_ns[r]));
+        cudaEventRecord(l.ev0, l.st);
         cudaMemcpyAsync(l.d_insts, l.h_insts, sizeof(InstDev) * ninst, cudaMemcpyHostToDevice, l.st);
         if (nitems) {
             cudaMemcpyAsync(l.d_items, l.h_items, sizeof(ServeItem) * nitems, cudaMemcpyHostToDevice, l.st);
