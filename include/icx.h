@@ -115,6 +115,17 @@ size_t icx_fastpfor_max_bytes(size_t n);
 /* Bytes of device workspace a decode, delta_decode or index call on n
  * integers needs (a 256-byte header plus look-back tile states). */
 size_t icx_workspace_bytes(size_t n);
+
+/* Where a decode of n integers puts its regions in a workspace of ws_bytes
+ * bytes (a diagnostic; the decoders compute the same).  out[0] = the largest
+ * length the workspace serves, out[1] = end of n's look-back states (from the
+ * start), out[2] = start of the page parse's records, out[3] = start of the
+ * SIMD-FastPFOR prepare kernel's records, out[4] = end of those plain regions,
+ * out[5] = start of the tagged scratch of the block-per-lane decoders (to the
+ * end).  Tagged regions (look-back states, the scratch) of any length the
+ * workspace serves never overlap plain regions of any other.  ICX_EINVAL if
+ * ws_bytes < icx_workspace_bytes(n) or out is NULL. */
+icx_status icx_workspace_layout(size_t n, size_t ws_bytes, size_t *out);
 /* Bytes of device workspace an encode call on n integers needs. */
 size_t icx_encode_workspace_bytes(size_t n);
 

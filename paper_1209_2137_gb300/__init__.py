@@ -65,6 +65,7 @@ def lib():
                 "icx_workspace_init": ([vp, sz, vp], i),
                 "icx_status_read": ([vp, vp, ctypes.POINTER(ctypes.c_int)], i),
                 "icx_workspace_set_wait_limit": ([vp, sz, ctypes.c_uint, vp], i),
+                "icx_workspace_layout": ([sz, sz, ctypes.POINTER(sz)], i),
                 "bp128_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
                 "fastpfor_index": ([vp, sz, sz, i, vp, vp, sz, vp], i),
                 "bp128_decode": ([vp, sz, vp, sz, i, i, vp, vp, sz, vp], i),
@@ -97,7 +98,7 @@ def lib():
 
 EXPORTED = ("icx_bp128_index_len", "icx_fastpfor_index_len", "icx_bp128_max_bytes", "icx_fastpfor_max_bytes",
             "icx_workspace_bytes", "icx_encode_workspace_bytes", "icx_workspace_init", "icx_status_read",
-            "icx_workspace_set_wait_limit",
+            "icx_workspace_set_wait_limit", "icx_workspace_layout",
             "bp128_index", "fastpfor_index", "bp128_decode", "fastpfor_decode", "bp128_intersect",
             "sorted_intersect", "delta_decode", "delta_encode",
             "bp128_encode", "fastpfor_encode", "icx_version", "icx_set_tuning", "icx_plan_create",

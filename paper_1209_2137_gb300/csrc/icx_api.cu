@@ -50,6 +50,18 @@ size_t icx_fastpfor_max_bytes(size_t n) {
 
 size_t icx_workspace_bytes(size_t n) { return icx::ws_total_bytes(n); }
 
+icx_status icx_workspace_layout(size_t n, size_t ws_bytes, size_t* out) {
+    if (!out || ws_bytes < icx::ws_total_bytes(n)) return ICX_EINVAL;
+    const size_t N = icx::ws_capacity(ws_bytes), plain = icx::ws_plain_base(ws_bytes);
+    out[0] = N;
+    out[1] = icx::kWsHeaderBytes + 32 * icx::ws_tiles(n);  // end of n's look-back states
+    out[2] = plain;                                        // page parse records
+    out[3] = plain + icx::ws_meta_bytes(n);                // prepare-kernel records
+    out[4] = out[3] + icx::ws_fp2_bytes(n);                // end of the plain regions
+    out[5] = (ws_bytes - icx::ws_blocklane_bytes(n)) / 256 * 256;  // tagged block-per-lane scratch
+    return ICX_OK;
+}
+
 size_t icx_encode_workspace_bytes(size_t n) {
     const size_t bp = enc_sizes_off(n) + round_up(4 * (metablocks(n) + 2), 256);
     const size_t fp = icx::fastpfor_encode_workspace_bytes(n);

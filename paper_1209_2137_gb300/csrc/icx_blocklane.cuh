@@ -669,9 +669,10 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
 
 // Scratch layout of a decode of n integers inside a workspace of ws_bytes
 // bytes at h: the last ws_blocklane_bytes(n) bytes (from a 256-byte
-// boundary).  Every region another decoder writes for a length m ends at
-// ws_unitmeta_end(m) <= ws_bytes - ws_blocklane_bytes(m), and the region
-// grows with the length, so no decoder sharing the workspace writes here.
+// boundary).  Every plain region any decoder writes for a length m the
+// workspace serves ends below ws_bytes - ws_blocklane_bytes(capacity) (the
+// layout in icx_device.cuh), and this region grows with the length, so only
+// tagged words of these decoders are ever written here.
 inline bl::Scratch blocklane_scratch(WsHeader* h, size_t n, size_t ws_bytes) {
     const size_t nb = n / 128, P = (nb + 31) / 32, Gn = (P + bl::kGroup - 1) / bl::kGroup;
     const size_t at = (ws_bytes - ws_blocklane_bytes(n)) / 256 * 256;

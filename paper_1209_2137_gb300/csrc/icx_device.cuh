@@ -44,27 +44,58 @@ struct BlockMeta {
 static_assert(sizeof(BlockMeta) == 16, "block meta");
 constexpr size_t kPageMetaWords = 36;  // arr_off[32] (page-relative), bad flag, pad
 
+// Workspace layout for a decode of n integers in a workspace of ws_bytes
+// bytes.  Regions that hold epoch-tagged words (read as "published" only when
+// their tag matches the current launch) never share bytes with regions that
+// hold plain data, whatever lengths share the workspace:
+//   - the header and the look-back tile states, sized for the largest length
+//     N the workspace serves (ws_capacity);
+//   - after them the plain regions for n: SIMD-FastPFOR block records, page
+//     records and per-16-block ranges (page parse), then the prepare
+//     kernel's per-block records and tile sums;
+//   - at the very end the tagged scratch of the block-per-lane decoders for
+//     n (it grows with n, so it stays above every plain region of any length
+//     up to N).
+__host__ __device__ inline size_t ws_round(size_t x) { return (x + 255) / 256 * 256; }
 __host__ __device__ inline size_t ws_tiles(size_t n) { return n / 2048 + 16; }
-__host__ __device__ inline size_t ws_blockmeta_off(size_t n) { return kWsHeaderBytes + 32 * ws_tiles(n); }
-__host__ __device__ inline size_t ws_pagemeta_off(size_t n) { return ws_blockmeta_off(n) + 16 * (n / 128 + 1); }
-__host__ __device__ inline size_t ws_unitmeta_off(size_t n) {
-    const size_t end = ws_pagemeta_off(n) + 4 * kPageMetaWords * ((n / 128 + 511) / 512 + 1);
-    return (end + 255) / 256 * 256;
+__host__ __device__ inline size_t ws_head_bytes(size_t n) { return ws_round(kWsHeaderBytes + 32 * ws_tiles(n)); }
+// page parse: one BlockMeta per block, kPageMetaWords per page, an 8-byte
+// range per unit of 16 blocks
+__host__ __device__ inline size_t ws_pagemeta_rel(size_t n) { return 16 * (n / 128 + 1); }
+__host__ __device__ inline size_t ws_unitmeta_rel(size_t n) {
+    return ws_round(ws_pagemeta_rel(n) + 4 * kPageMetaWords * ((n / 128 + 511) / 512 + 1));
 }
-// per unit of 16 blocks: page-relative offset and size of its packed low bits
-__host__ __device__ inline size_t ws_unitmeta_end(size_t n) {
-    const size_t end = ws_unitmeta_off(n) + 8 * (n / 2048 + 2);
-    return (end + 255) / 256 * 256;
+__host__ __device__ inline size_t ws_meta_bytes(size_t n) { return ws_round(ws_unitmeta_rel(n) + 8 * (n / 2048 + 2)); }
+// prepare kernel: 32 bytes per block, 16 per tile of 256 blocks
+__host__ __device__ inline size_t ws_fp2_tiles_rel(size_t n) { return 32 * (n / 128 + 1); }
+__host__ __device__ inline size_t ws_fp2_bytes(size_t n) {
+    return ws_round(ws_fp2_tiles_rel(n) + 16 * ((n / 128 + 255) / 256 + 1));
 }
-// Two-phase SIMD-BP128 decoding: per 128-integer block four tagged 64-bit
-// words (block sums), per pair of metablocks two groups of four (pair total,
-// pair prefix), per group of 64 pairs one group of four (look-back state)
-// and a 32-bit counter.
+// Two-phase block-per-lane decoding: per 128-integer block four tagged
+// 64-bit words (block sums), per pair of metablocks two groups of four (pair
+// total, pair prefix), per group of 64 pairs one group of four (look-back
+// state) and a 32-bit counter.
 __host__ __device__ inline size_t ws_blocklane_bytes(size_t n) {
     const size_t nb = n / 128, P = ((nb + 15) / 16 + 1) / 2, Gn = (P + 63) / 64;
-    return (32 * (nb + 1) + 64 * (P + 1) + 36 * (Gn + 1) + 255) / 256 * 256;
+    return ws_round(32 * (nb + 1) + 64 * (P + 1) + 36 * (Gn + 1));
 }
-__host__ __device__ inline size_t ws_total_bytes(size_t n) { return ws_unitmeta_end(n) + ws_blocklane_bytes(n); }
+__host__ __device__ inline size_t ws_total_bytes(size_t n) {
+    return ws_head_bytes(n) + ws_meta_bytes(n) + ws_fp2_bytes(n) + ws_blocklane_bytes(n);
+}
+// The largest length a workspace of ws_bytes serves (every size above grows
+// with n).
+__host__ __device__ inline size_t ws_capacity(size_t ws_bytes) {
+    size_t lo = 0, hi = (size_t)1 << 44;
+    if (ws_total_bytes(0) > ws_bytes) return 0;
+    while (lo < hi) {
+        const size_t mid = lo + (hi - lo + 1) / 2;
+        if (ws_total_bytes(mid) <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+// Start of the plain regions in a workspace of ws_bytes.
+__host__ __device__ inline size_t ws_plain_base(size_t ws_bytes) { return ws_head_bytes(ws_capacity(ws_bytes)); }
 
 // A device wait that sees no progress for this long gives up with ETIMEOUT.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;

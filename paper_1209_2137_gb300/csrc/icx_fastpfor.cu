@@ -519,9 +519,10 @@ static cudaError_t launch_fp(const uint8_t* in, size_t in_bytes, uint32_t* out, 
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     char* ws = reinterpret_cast<char*>(h);
-    BlockMeta* meta = reinterpret_cast<BlockMeta*>(ws + ws_blockmeta_off(n));
-    uint32_t* pmeta = reinterpret_cast<uint32_t*>(ws + ws_pagemeta_off(n));
-    uint2* umeta = reinterpret_cast<uint2*>(ws + ws_unitmeta_off(n));
+    const size_t plain = ws_plain_base(ws_bytes);
+    BlockMeta* meta = reinterpret_cast<BlockMeta*>(ws + plain);
+    uint32_t* pmeta = reinterpret_cast<uint32_t*>(ws + plain + ws_pagemeta_rel(n));
+    uint2* umeta = reinterpret_cast<uint2*>(ws + plain + ws_unitmeta_rel(n));
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, U = (nb + 15) / 16;
     if (LAYOUT == ICX_FMT_PAPER && DELTA != ICX_DELTA_NONE && g_fp_blocklane == 2)
         return launch_fastpfor_two_kernel(DELTA, in, in_bytes, out, n, index, meta, pmeta, umeta, h, ws_bytes, s);

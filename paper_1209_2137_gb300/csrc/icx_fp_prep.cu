@@ -670,9 +670,11 @@ static cudaError_t launch_fp2_t(const uint8_t* in, size_t in_bytes, uint32_t* ou
                                 cudaStream_t s) {
     const size_t nb = n / 128, P = (nb + kBlocksPerPage - 1) / kBlocksPerPage, Q = (nb + 31) / 32;
     const size_t T = (nb + fp2::kPrepThreads - 1) / fp2::kPrepThreads;
-    const bl::Scratch sc = blocklane_scratch(h, n, ws_bytes);
-    uint4* rec = reinterpret_cast<uint4*>(sc.bst);        // 32 bytes per block
-    uint4* tiles = reinterpret_cast<uint4*>(sc.ptot);     // 16 bytes per tile (8 pairs)
+    // plain data (no tagged words): its own workspace region after the page
+    // parse's records
+    char* fp2 = reinterpret_cast<char*>(h) + ws_plain_base(ws_bytes) + ws_meta_bytes(n);
+    uint4* rec = reinterpret_cast<uint4*>(fp2);                           // 32 bytes per block
+    uint4* tiles = reinterpret_cast<uint4*>(fp2 + ws_fp2_tiles_rel(n));  // 16 bytes per tile (8 pairs)
     if (P > 0) {
         const cudaError_t em = launch_fastpfor_meta(in, in_bytes, n, index, meta, pmeta, umeta, h, s);
         if (em != cudaSuccess) return em;

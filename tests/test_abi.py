@@ -152,3 +152,25 @@ def test_static_decode_refusals_before_any_device_call(lib):
     assert fn(a16, 1 << 20, a16, 2049 * 16, icx.DELTA_4, icx.FMT_PAPER, None, None, None) == icx.EINVAL  # M > 1, no index
     assert fn(a16, 64, a16, (1 << 28) + 1, icx.DELTA_1, icx.FMT_PAPER, a16, None, None) == icx.ENOSPC
     assert fn(None, 0, None, 0, icx.DELTA_1, icx.FMT_PAPER, None, None, None) == icx.OK  # nothing to decode
+
+
+def test_workspace_layout_keeps_tagged_and_plain_regions_apart(lib):
+    # decodes of different lengths share a workspace: the look-back states and
+    # the block-per-lane scratch (epoch-tagged words) of every length it serves
+    # never overlap the plain records of any other length
+    import paper_1209_2137_gb300 as icx
+    L = icx.lib()
+    out = (ctypes.c_size_t * 6)()
+    for cap in (128, 4096 + 77, 65536 * 3 + 5, 1 << 26, 56273636):
+        ws = icx.workspace_bytes(cap)
+        assert L.icx_workspace_layout(cap, ws - 1, out) == icx.EINVAL
+        lens = sorted(m for m in {1, 129, 2048, 4096 * 5 + 3, 65537, cap // 3, cap // 2 + 1, cap} if m <= cap)
+        regs = {}
+        for n in lens:
+            assert L.icx_workspace_layout(n, ws, out) == icx.OK
+            N, states_end, plain, fp2, plain_end, scratch = list(out)
+            assert N >= cap and states_end <= plain <= fp2 <= plain_end <= scratch <= ws
+            regs[n] = (states_end, plain, plain_end, scratch)
+        for n, (se, _, _, sc) in regs.items():
+            for m, (_, pl, pe, _) in regs.items():
+                assert se <= pl and pe <= sc, (n, m)  # n's tagged regions vs m's plain ones
