@@ -26,6 +26,7 @@ constexpr uint32_t kHdr = 256;
 
 struct Hdr {
     unsigned long long bar[2 * kW];  // two staging barriers per warp (left and right end of its ring)
+    unsigned long long wait_limit;   // limit of the waits on published values (ns), read once
     uint32_t last;                   // this CTA finished the launch last
 };
 static_assert(sizeof(Hdr) <= kHdr, "header");
@@ -80,12 +81,12 @@ __device__ __forceinline__ bool ld_tagged(const unsigned long long* p, uint32_t 
 // Waits (bounded) until the NL words at p carry `tag`; returns their values.
 template <int NL, uint32_t IGN = 0>
 __device__ __forceinline__ uint4 wait_tagged(const unsigned long long* p, uint32_t tag, WsHeader* h,
-                                             uint32_t* t0 = nullptr) {
+                                             const unsigned long long* limit, uint32_t* t0 = nullptr) {
     uint4 v;
     if (ld_tagged<NL, IGN>(p, tag, v, t0)) return v;
     const unsigned long long ts = globaltimer();
     while (!ld_tagged<NL, IGN>(p, tag, v, t0)) {
-        if (globaltimer() - ts > wait_limit_ns(h)) {
+        if (globaltimer() - ts > *limit) {
             set_error(h, ICX_ETIMEOUT);
             break;
         }
@@ -371,7 +372,10 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
     }
     fence_mbar_init();
     // the first CTA to start zeroes the group counters, then raises aux[3]
-    if (threadIdx.x == 0) S.last = atomicAdd(&h->aux[4], 1u) == 0 ? 1u : 0u;
+    if (threadIdx.x == 0) {
+        S.last = atomicAdd(&h->aux[4], 1u) == 0 ? 1u : 0u;
+        S.wait_limit = wait_limit_ns(h);
+    }
     __syncthreads();
     if (S.last) {
         for (uint32_t i = threadIdx.x; i < Gn; i += blockDim.x) sc.gcnt[i] = 0;
@@ -464,14 +468,14 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
         bool ok0 = true, ok1 = true;
         if (p0 < P) ok0 = ld_tagged<NL>(sc.ptot + 4 * (size_t)p0, tagA, v0);
         if (p0 + 1 < P) ok1 = ld_tagged<NL>(sc.ptot + 4 * (size_t)(p0 + 1), tagA, v1);
-        if (!ok0) v0 = wait_tagged<NL>(sc.ptot + 4 * (size_t)p0, tagA, h);
-        if (!ok1) v1 = wait_tagged<NL>(sc.ptot + 4 * (size_t)(p0 + 1), tagA, h);
+        if (!ok0) v0 = wait_tagged<NL>(sc.ptot + 4 * (size_t)p0, tagA, h, &S.wait_limit);
+        if (!ok1) v1 = wait_tagged<NL>(sc.ptot + 4 * (size_t)(p0 + 1), tagA, h, &S.wait_limit);
         const uint4 ls = add4(v0, v1);
         const uint4 li = warp_scan_carry<DELTA>(ls, lane);
         const uint4 agg = shfl4(li, 31);
         if (lane < NL)
             st_relaxed(sc.gst + 4 * (size_t)g + lane, ((unsigned long long)(g ? tagA : tagI) << 32) | comp(agg, lane));
-        const uint4 ex = lookback_resolve_at<NL>(sc.gst, h, epoch, g, agg);
+        const uint4 ex = lookback_resolve_at<NL>(sc.gst, h, epoch, g, agg, true, &S.wait_limit);
         const uint4 e0 = add4(ex, sub4(li, ls));
         if (p0 < P) st_tagged<NL>(sc.pre + 4 * (size_t)p0, tagI, e0);
         if (p0 + 1 < P) st_tagged<NL>(sc.pre + 4 * (size_t)(p0 + 1), tagI, add4(e0, v0));
@@ -564,7 +568,7 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
                 if (lane == 0) {
                     const unsigned long long t0 = globaltimer();
                     while (ld_acquire_u32(&h->aux[3]) != epoch + 1u) {
-                        if (globaltimer() - t0 > wait_limit_ns(h)) {
+                        if (globaltimer() - t0 > S.wait_limit) {
                             set_error(h, ICX_ETIMEOUT);
                             break;
                         }
@@ -583,10 +587,10 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
             if (__shfl_sync(FULL, last, 0)) scan_group(g);
         } else if (kc == 1) {
             // ------------------------------------------------------ B task
-            if (!__all_sync(FULL, pre_ok)) pre_c = wait_tagged<NL>(sc.pre + 4 * (size_t)pc, tagI, h);
+            if (!__all_sync(FULL, pre_ok)) pre_c = wait_tagged<NL>(sc.pre + 4 * (size_t)pc, tagI, h, &S.wait_limit);
             if (!bs_ok) {
                 uint32_t t0 = 0;
-                bs_c = wait_tagged<NL, kSumFlag>(sc.bst + 4 * (32 * (size_t)pc + lane), tagA, h, &t0);
+                bs_c = wait_tagged<NL, kSumFlag>(sc.bst + 4 * (32 * (size_t)pc + lane), tagA, h, &S.wait_limit, &t0);
                 bflag = t0 & kSumFlag;
             }
             const uint4 bi = warp_scan_carry<DELTA>(bs_c, lane);
@@ -606,7 +610,7 @@ __device__ __forceinline__ void run(const C& codec, const uint8_t* __restrict__ 
             // ---------------------------------------- the Variable Byte tail
             // its carry is the inclusive prefix of the last group
             uint4 carry = make_uint4(0, 0, 0, 0);
-            if (P > 0) carry = wait_tagged<NL>(sc.gst + 4 * (size_t)(Gn - 1), tagI, h);
+            if (P > 0) carry = wait_tagged<NL>(sc.gst + 4 * (size_t)(Gn - 1), tagI, h, &S.wait_limit);
             uint32_t* scratch = reinterpret_cast<uint32_t*>(rest);
             const uint64_t tstart = codec.tail_start();
             uint4 v = make_uint4(0, 0, 0, 0);

@@ -353,7 +353,7 @@ constexpr int kLookbackRows = 1;
 // inclusive prefix.  Whole warp.
 template <int NL, int R = kLookbackRows>
 __device__ uint4 lookback_resolve_at(unsigned long long* st, WsHeader* h, uint32_t epoch, uint32_t tile, uint4 agg,
-                                     bool publish = true) {
+                                     bool publish = true, const unsigned long long* limit = nullptr) {
     static_assert(NL == 1 || NL == 4, "chains");
     const int lane = threadIdx.x & 31;
     const uint32_t tagA = (epoch << 2) | 1u, tagP = (epoch << 2) | 2u;
@@ -404,7 +404,7 @@ __device__ uint4 lookback_resolve_at(unsigned long long* st, WsHeader* h, uint32
         }
         if (wait) {
             if (t0 == 0) t0 = globaltimer();
-            if (globaltimer() - t0 > wait_limit_ns(h)) {
+            if (globaltimer() - t0 > (limit ? *limit : wait_limit_ns(h))) {
                 if (lane == 0) set_error(h, ICX_ETIMEOUT);
                 break;
             }
