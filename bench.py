@@ -329,6 +329,7 @@ def run_gpu(args, world, rank, local):
     intersect = None if args.skip_intersect else run_intersect(args, streams, arrays, out, ws, flush_l2, world)
     bp32 = None if args.skip_bp32 else run_bp32(args, arrays, out, ws, flush_l2, world)
     encode = None if args.skip_encode else run_encode(args, arrays, dev, flush_l2, world)
+    aux = None if args.skip_aux else run_aux(args, streams, arrays, dev, ws, flush_l2, world)
     batched = serving = None
     if not args.skip_batch:
         del out
@@ -356,6 +357,7 @@ def run_gpu(args, world, rank, local):
         "intersect": intersect,
         "bp32": bp32,
         "encode": encode,
+        "aux": aux,
         "batched": batched,
         "serving": serving,
         "gpu_launches": launches_per_step * K,
@@ -454,7 +456,7 @@ def run_exceptions(args, out, ws, flush_l2, world):
     import paper_1209_2137_gb300 as icx
     from paper_1209_2137_gb300 import workloads as W
 
-    x = W.workload_exceptions()
+    x = W.workload_exceptions(args.exceptions_n) if args.exceptions_n else W.workload_exceptions()
     xt = torch.from_numpy(x).to(out.device)
     if out.numel() < x.size or ws.n < x.size:  # a reduced main workload: buffers of this size
         out = torch.empty(x.size, dtype=torch.uint32, device=out.device)
@@ -486,6 +488,75 @@ def run_exceptions(args, out, ws, flush_l2, world):
                       "achieved_gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
     res["note"] = "the GPU encoders write the oracle's bytes (tests), so bits_per_int is the oracle's"
     log(f"[bench] exception-heavy: SIMD-FastPFOR {res['SIMD-FastPFOR']}, SIMD-BP128 {res['SIMD-BP128']}")
+    return res
+
+
+# ------------------------------------------------------------------ aux --
+
+def run_aux(args, streams, arrays, dev, ws, flush_l2, world):
+    """The remaining calls of the boundary on the uniform array: differential
+    decoding alone (Sec. 3: prefix sums with stride 1 and 4 over 4-byte
+    differences; roofline bytes 8 per integer), differential encoding, and
+    the index walks over a SIMD-BP128 and a SIMD-FastPFOR stream (serial
+    walks over the metablock / page headers)."""
+    import torch
+
+    import paper_1209_2137_gb300 as icx
+
+    peak, _ = peaks()
+    x = arrays["uniform"]
+    n = x.size
+    xt = torch.from_numpy(x).to(dev)
+    res = {"workload": f"uniform n={n}"}
+
+    def timed(fn, alg):
+        for _ in range(args.warmup):
+            flush_l2()
+            fn()
+        steps = max(3, min(args.steps, 20))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush_l2()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world)
+        r = {"ms": round(ms, 4), "gints_s": round(n / (ms / 1e3) / 1e9, 1)}
+        if alg:
+            r["achieved_gbs"] = round(alg / (ms / 1e3) / 1e9, 1)
+            r["frac"] = round(alg / (ms / 1e3) / 1e9 / peak, 4)
+        return r
+
+    out = torch.empty_like(xt)
+    for delta in (1, 4):
+        d = icx.delta_encode(xt, delta)
+        icx.delta_decode(d, delta, out=out, workspace=ws)
+        ws.raise_status("delta decode")
+        if not torch.equal(out, xt):
+            raise SystemExit("delta decode: verification failed")
+        res[f"delta_decode_d{delta}"] = timed(lambda: icx.delta_decode(d, delta, out=out, workspace=ws), 8 * n)
+        res[f"delta_encode_d{delta}"] = timed(lambda: icx.delta_encode(xt, delta, out=out), 8 * n)
+        del d
+    for s in streams:
+        if s["array"] != "uniform" or s["delta"] != 1 or s["fmt"] != 0:
+            continue
+        enc = s["enc"]
+        ix = torch.empty_like(enc.index)
+        if s["codec"] == "bp128":
+            fn = lambda: icx.bp128_index(enc.data, enc.n, 0, index=ix, workspace=ws)
+        else:
+            fn = lambda: icx.fastpfor_index(enc.data, enc.n, index=ix, workspace=ws)
+        fn()
+        ws.raise_status("index walk")
+        if not torch.equal(ix, enc.index):
+            raise SystemExit(f"{s['label']} index walk: verification failed")
+        r = timed(fn, None)
+        r["entries"] = int(enc.index.numel())
+        res[f"index_{s['codec']}"] = r
+    del xt, out
+    torch.cuda.empty_cache()
+    log("[bench] aux: " + ", ".join(f"{k} {v['ms']} ms" for k, v in res.items() if isinstance(v, dict)))
     return res
 
 
@@ -941,6 +1012,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fastpfor", action="store_true")
     ap.add_argument("--skip-encode", action="store_true")
+    ap.add_argument("--skip-aux", action="store_true", help="skip the prefix-sum and index-walk timings")
     ap.add_argument("--e2e-streams", type=int, default=3, help="CUDA streams the end-to-end decodes rotate over")
     ap.add_argument("--extra-none", action="store_true", help="also time decodes without differential decoding")
     ap.add_argument("--n", type=int, default=0, help="reduced workload: uniform array of n integers only")
@@ -950,6 +1022,7 @@ def main():
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="library tuning key (icx_set_tuning), repeatable")
     ap.add_argument("--skip-exceptions", action="store_true", help="skip the exception-heavy decode")
+    ap.add_argument("--exceptions-n", type=int, default=0, help="integers of the exception-heavy array (0: 2^26)")
     ap.add_argument("--skip-intersect", action="store_true", help="skip the decode-into-intersection leg")
     ap.add_argument("--skip-bp32", action="store_true", help="skip the scalar-layout (BP32, FastPFOR) decodes")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched posting-list decode")
