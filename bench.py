@@ -869,15 +869,16 @@ def run_serving(args, pool, L):
         nreq = int(rate * args.serve_seconds) if rate > 0 else args.serve_saturation
         z = W.splitmix64(W.SEED_BASE + 5, 100 * i, 3 * nreq)
         u = ((z[:nreq] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
-        arrival = np.cumsum(-np.log(u) / rate * 1e9).astype(np.uint64)
+        if rate > 0:
+            arrival = np.cumsum(-np.log(u) / rate * 1e9).astype(np.uint64)
+        else:  # closed loop at saturation: every request waiting at the start
+            arrival = np.zeros(nreq, dtype=np.uint64)
         k = 2 + (z[nreq:2 * nreq] % np.uint64(7)).astype(np.int64)
         offs = np.zeros(nreq + 1, dtype=np.int64)
         np.cumsum(k, out=offs[1:])
         zz = W.splitmix64(W.SEED_BASE + 6, 100 * i, int(offs[-1]))
         uu = ((zz >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
         ids = by_rank[np.minimum(np.searchsorted(cum, uu), len(L) - 1)].astype(np.uint32)
-        if rate <= 0:  # closed loop at saturation: every request waiting at the start
-            arrival = np.zeros(nreq, dtype=np.uint64)
         lat, st, _ = sv.run(arrival, offs, ids)
         ms = lat.astype(np.float64) / 1e6
         span = float(arrival[-1]) / 1e9 if nreq else 0.0
@@ -893,7 +894,7 @@ def run_serving(args, pool, L):
                      "ints_per_request": round(st["ints"] / max(1, nreq)), "batches": int(st["batches"]),
                      "mean_batch": round(nreq / max(1, st["batches"]), 2), "max_batch": int(st["max_batch"]),
                      "max_queue": int(st["max_queue"]), "peak_buffer_gb": round(st["peak_bytes"] / 2**30, 3)})
-        log(f"[bench] serve {rate} req/s: p50 {rows[-1]['p50_ms']} ms p99 {rows[-1]['p99_ms']} ms, "
+        log(f"[bench] serve {rows[-1]['rate_req_s']} req/s: p50 {rows[-1]['p50_ms']} ms p99 {rows[-1]['p99_ms']} ms, "
             f"{rows[-1]['gints_s']} Gints/s, {rows[-1]['mean_batch']} req/batch")
     sv.close()
     return {"workload": "the batch's pool resident in HBM; Poisson arrivals; k ~ U{2..8} lists per request, "
