@@ -302,7 +302,8 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *       lane): output path of the two-pass decoders;
  *   "bp128.blocklane_ctas" = CTAs of their persistent grid (0 = all resident);
  *   "bp128.blocklane_lead" = pairs summed before the first decode task
- *       (0 = two per resident warp; at least 128);
+ *       (0 = every pair with stride 4, two per resident warp with stride 1;
+ *       at least 128);
  *   "bp128.blocklane_sum_warps" = warps per CTA that only sum (0 = every
  *       warp takes both kinds of task).
  * The bp128.blocklane_* settings apply to both two-pass decoders.

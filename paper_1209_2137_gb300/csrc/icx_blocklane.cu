@@ -19,7 +19,9 @@
 // once.  Warps take tasks from one counter: A tasks alone
 // for a lead of pairs, then A and B tasks alternately (A runs a lead ahead of
 // B), then the remaining B tasks, so the summing (compute bound) overlaps the
-// stores (bandwidth bound).  Every task waits only for tasks taken before
+// stores (bandwidth bound).  With stride 4 the default lead is every pair:
+// all sums first, then every decode task finds its carry published.  Every
+// task waits only for tasks taken before
 // it, and every published value is a set of 64-bit words tagged with the
 // launch epoch, so readers need no fences.
 #include "icx_blocklane.cuh"
@@ -202,8 +204,13 @@ static int g_blocklane_ctas = 0;  // CTAs of the persistent grid (0: as many as 
 
 void set_bp128_blocklane_ctas(int v) { g_blocklane_ctas = v > 0 ? v : 0; }
 
-// Pairs summed before the first decode task (0: two per resident warp; at
-// least 128, which keeps every task's dependencies before it).
+// Pairs summed before the first decode task (0: every pair with stride 4,
+// two per resident warp with stride 1; at least 128, which keeps every
+// task's dependencies before it).  Measured on the 2^26 uniform and the
+// clustered arrays (ms, default / two per warp / 2048): stride 4 summing
+// every pair first 0.0815 / 0.0845 / 0.0960 and 0.0692 / 0.0758 / 0.0856;
+// stride 1 two per warp 0.0819 (0.0836 with every pair first) and 0.0717
+// (0.0717).
 static int g_blocklane_lead = 0;
 
 void set_bp128_blocklane_lead(int v) { g_blocklane_lead = v > 0 ? v : 0; }
@@ -239,7 +246,9 @@ static cudaError_t launch_blocklane_t(const uint8_t* in, size_t in_bytes, uint32
     const size_t resident = (size_t)blocks_per_sm * sms;
     size_t G = max((size_t)1, min(resident, (P + bl::kW - 1) / bl::kW));
     if (g_blocklane_ctas > 0 && (size_t)g_blocklane_ctas < G) G = (size_t)g_blocklane_ctas;
-    const size_t lead = max((size_t)128, g_blocklane_lead > 0 ? (size_t)g_blocklane_lead : 2 * G * bl::kW);
+    const size_t lead = max((size_t)128, g_blocklane_lead > 0        ? (size_t)g_blocklane_lead
+                                         : DELTA == ICX_DELTA_4 ? P
+                                                                : 2 * G * bl::kW);
     kern<<<(int)G, bl::kW * 32, smem, s>>>(in, in_bytes, out, n, index, h, blocklane_scratch(h, n, ws_bytes),
                                             (uint32_t)(n - 128 * nb), (uint32_t)min(lead, (size_t)0xFFFFFFFFu),
                                             (uint32_t)g_blocklane_sumw);
