@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstddef>
+#include <type_traits>
 
 #include "icx_device.cuh"
 #include "icx_tile.cuh"
@@ -257,6 +258,42 @@ struct NoPatch {
     __device__ __forceinline__ void operator()(uint4&, int) {}
 };
 
+// Pass-A block sum with four fields per window step and every width of the
+// warp in 4..8 (b = 0 for lanes without a block): per residue, one masked
+// add folds fields 0 + 1 into bits [0, b + 1) and fields 2 + 3 into bits
+// [2b, 3b + 1) of a 32-bit word, and the eight steps of the block add these
+// words up.  Each half then holds at most 16 (2^b - 1) < 2^(b + 4) <= 2^(2b),
+// so the low half never carries into the high one, and the high half ends
+// below bit 3b + 4 <= 28; the two halves are added once at the end.  The
+// same integers as adding the 32 fields one by one, with five operations
+// per residue and step instead of eleven.
+template <class Rows, class Mid>
+__device__ __forceinline__ void sum_block_swar(const Rows& rows, Walk& w, Mid& mid) {
+    const uint32_t b = w.b, step = 4 * b, m2 = w.mask | (w.mask << (2 * b));
+    uint4 s = make_uint4(0, 0, 0, 0);
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 4) {
+            uint4 x;
+            x.x = __funnelshift_r(w.r0.x, w.r1.x, w.sh);
+            x.y = __funnelshift_r(w.r0.y, w.r1.y, w.sh);
+            x.z = __funnelshift_r(w.r0.z, w.r1.z, w.sh);
+            x.w = __funnelshift_r(w.r0.w, w.r1.w, w.sh);
+            w.sh += step;
+            rows.advance(w.r0, w.r1, w.sh, w.nxt);
+            s.x += (x.x & m2) + ((x.x >> b) & m2);
+            s.y += (x.y & m2) + ((x.y >> b) & m2);
+            s.z += (x.z & m2) + ((x.z >> b) & m2);
+            s.w += (x.w & m2) + ((x.w >> b) & m2);
+        }
+        if (c == 0) mid();
+    }
+    const uint32_t lo = (1u << (2 * b)) - 1u, hs = 2 * b;
+    w.acc = add4(w.acc, make_uint4((s.x & lo) + (s.x >> hs), (s.y & lo) + (s.y >> hs), (s.z & lo) + (s.z >> hs),
+                                   (s.w & lo) + (s.w >> hs)));
+}
+
 // The 32 fields of the lane's block, FPS fields per window step: with every
 // width of the pair at most 32 / FPS, the FPS fields from the current bit
 // offset all lie in one 32-bit funnel shift of the window, so the window
@@ -264,6 +301,12 @@ struct NoPatch {
 // emitted.
 template <int DELTA, bool DECODE, int STORE, int FPS, class Rows, class Mid, class Patch>
 __device__ __forceinline__ void walk_block(const Rows& rows, Walk& w, Mid& mid, Patch& patch) {
+    if constexpr (!DECODE && FPS == 4 && std::is_same<Patch, NoPatch>::value) {
+        if (__reduce_max_sync(FULL, w.b) <= 8u && __reduce_min_sync(FULL, w.b ? w.b : 32u) >= 4u) {
+            sum_block_swar(rows, w, mid);
+            return;
+        }
+    }
     const uint32_t b2 = 2 * w.b, b3 = 3 * w.b, step = FPS * w.b;
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
