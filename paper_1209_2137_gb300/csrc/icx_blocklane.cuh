@@ -258,23 +258,46 @@ struct NoPatch {
     __device__ __forceinline__ void operator()(uint4&, int) {}
 };
 
-// Pass-A block sum with four fields per window step and every width of the
-// warp in 4..8 (b = 0 for lanes without a block): per residue, one masked
-// add folds fields 0 + 1 into bits [0, b + 1) and fields 2 + 3 into bits
-// [2b, 3b + 1) of a 32-bit word, and the eight steps of the block add these
-// words up.  Each half then holds at most 16 (2^b - 1) < 2^(b + 4) <= 2^(2b),
-// so the low half never carries into the high one, and the high half ends
-// below bit 3b + 4 <= 28; the two halves are added once at the end.  The
-// same integers as adding the 32 fields one by one, with five operations
-// per residue and step instead of eleven.
-template <class Rows, class Mid>
+// Pass-A block sums that add several fields per operation (every width of
+// the warp at most 8; b = 0 for lanes without a block).  Per residue and
+// window step x holds the next fields at bits 0, b, 2b, ...:
+//   MODE 4 (widths 4..8, four fields a step): one masked add folds fields
+//     0 + 1 into bits [0, b + 1) and 2 + 3 into [2b, 3b + 1); the eight
+//     steps add these words up.  Each half then holds at most
+//     16 (2^b - 1) < 2^(b + 4) <= 2^(2b), so the low half never carries into
+//     the high one, and the high half ends below bit 3b + 4 <= 28; the two
+//     halves are added once at the end;
+//   MODE 5 (widths 0..8, four fields a step): the same fold, its two halves
+//     added at every step (b + 1 <= 2b bits each);
+//   MODE 8 (widths 0..4, eight fields a step): pairs fold into bits 0, 2b,
+//     4b, 6b (b + 1 bits each), the pairs into quads at 0 and 4b (b + 2 <= 4b
+//     bits each), and the quads are added at every step.
+// The same integers as adding the 32 fields one by one (mod 2^32 like
+// them), with 5, 8 and 10 operations per residue and step instead of 11,
+// 11 and 23.
+template <int MODE, class Rows, class Mid>
 __device__ __forceinline__ void sum_block_swar(const Rows& rows, Walk& w, Mid& mid) {
-    const uint32_t b = w.b, step = 4 * b, m2 = w.mask | (w.mask << (2 * b));
+    constexpr int FPS = MODE == 8 ? 8 : 4;
+    const uint32_t b = w.b, step = FPS * b, b2 = 2 * b, b4 = 4 * b;
+    const uint32_t m2 = w.mask | (w.mask << b2), lo = w.mask | (w.mask << b);  // lo: the low 2b bits
+    // (b <= 4 in MODE 8, so these shifts stay below 32)
+    const uint32_t mE = MODE == 8 ? m2 | (m2 << b4) : 0u, mQ = MODE == 8 ? lo | (lo << b4) : 0u,
+                   m4 = MODE == 8 ? lo | (lo << b2) : 0u;
+    auto fold = [&](uint32_t x) -> uint32_t {
+        if constexpr (MODE == 8) {
+            const uint32_t s1 = (x & mE) + ((x >> b) & mE);
+            const uint32_t s2 = (s1 & mQ) + ((s1 >> b2) & mQ);
+            return (s2 & m4) + (s2 >> b4);
+        } else {
+            const uint32_t t = (x & m2) + ((x >> b) & m2);
+            return MODE == 4 ? t : (t & lo) + (t >> b2);
+        }
+    };
     uint4 s = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
 #pragma unroll
-        for (int i = 0; i < 8; i += 4) {
+        for (int i = 0; i < 8; i += FPS) {
             uint4 x;
             x.x = __funnelshift_r(w.r0.x, w.r1.x, w.sh);
             x.y = __funnelshift_r(w.r0.y, w.r1.y, w.sh);
@@ -282,16 +305,17 @@ __device__ __forceinline__ void sum_block_swar(const Rows& rows, Walk& w, Mid& m
             x.w = __funnelshift_r(w.r0.w, w.r1.w, w.sh);
             w.sh += step;
             rows.advance(w.r0, w.r1, w.sh, w.nxt);
-            s.x += (x.x & m2) + ((x.x >> b) & m2);
-            s.y += (x.y & m2) + ((x.y >> b) & m2);
-            s.z += (x.z & m2) + ((x.z >> b) & m2);
-            s.w += (x.w & m2) + ((x.w >> b) & m2);
+            s.x += fold(x.x);
+            s.y += fold(x.y);
+            s.z += fold(x.z);
+            s.w += fold(x.w);
         }
         if (c == 0) mid();
     }
-    const uint32_t lo = (1u << (2 * b)) - 1u, hs = 2 * b;
-    w.acc = add4(w.acc, make_uint4((s.x & lo) + (s.x >> hs), (s.y & lo) + (s.y >> hs), (s.z & lo) + (s.z >> hs),
-                                   (s.w & lo) + (s.w >> hs)));
+    if constexpr (MODE == 4)
+        s = make_uint4((s.x & lo) + (s.x >> b2), (s.y & lo) + (s.y >> b2), (s.z & lo) + (s.z >> b2),
+                       (s.w & lo) + (s.w >> b2));
+    w.acc = add4(w.acc, s);
 }
 
 // The 32 fields of the lane's block, FPS fields per window step: with every
@@ -299,12 +323,29 @@ __device__ __forceinline__ void sum_block_swar(const Rows& rows, Walk& w, Mid& m
 // offset all lie in one 32-bit funnel shift of the window, so the window
 // moves once per FPS fields.  `patch(f, r)` may change field r before it is
 // emitted.
-template <int DELTA, bool DECODE, int STORE, int FPS, class Rows, class Mid, class Patch>
+//
+// Pass A without a patch takes sum_block_swar when the widths allow: MODE 4
+// always, MODES 8 and 5 only with SMALL.  (With all three the SIMD-BP128
+// stride-1 decoder spills registers and measured 0.0819 against 0.0778 ms
+// on 2^26 integers; the SIMD-FastPFOR prepare kernel, whose widths are
+// smaller, gained 0.1126 -> 0.1090 ms on the clustered array.)
+template <int DELTA, bool DECODE, int STORE, int FPS, bool SMALL = false, class Rows, class Mid, class Patch>
 __device__ __forceinline__ void walk_block(const Rows& rows, Walk& w, Mid& mid, Patch& patch) {
     if constexpr (!DECODE && FPS == 4 && std::is_same<Patch, NoPatch>::value) {
-        if (__reduce_max_sync(FULL, w.b) <= 8u && __reduce_min_sync(FULL, w.b ? w.b : 32u) >= 4u) {
-            sum_block_swar(rows, w, mid);
+        const uint32_t mx = __reduce_max_sync(FULL, w.b);
+        if (SMALL && mx <= 4u) {
+            sum_block_swar<8>(rows, w, mid);
             return;
+        }
+        if (mx <= 8u) {
+            if (__reduce_min_sync(FULL, w.b ? w.b : 32u) >= 4u) {
+                sum_block_swar<4>(rows, w, mid);
+                return;
+            }
+            if (SMALL) {
+                sum_block_swar<5>(rows, w, mid);
+                return;
+            }
         }
     }
     const uint32_t b2 = 2 * w.b, b3 = 3 * w.b, step = FPS * w.b;

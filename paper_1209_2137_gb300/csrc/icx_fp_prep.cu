@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(fp2::kPrepThreads, 4)
         NoMid nm;
         if (maxb) {
             if (maxb <= 8)
-                walk_block<DELTA, false, 0, 4>(rows, w, nm, np);
+                walk_block<DELTA, false, 0, 4, true>(rows, w, nm, np);
             else if (maxb <= 16)
                 walk_block<DELTA, false, 0, 2>(rows, w, nm, np);
             else
