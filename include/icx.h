@@ -297,6 +297,11 @@ icx_status fastpfor_encode(const uint32_t *d_x, size_t n, icx_delta delta, icx_l
  *       parse; 0: the tile decoder with a chained look-back (-1 = default);
  *   "fastpfor.stream_warps" = 4, 5 or 6 warps per CTA of the SIMD-FastPFOR
  *       stream kernel (0 = default: 4 for stride 1, 6 for stride 4);
+ *   "fastpfor.chain_overlap" = bits 0, 1, 2: the prepare, scan, stream
+ *       kernel of fastpfor.blocklane = 2 is launched as a programmatic
+ *       dependent, so it is scheduled while the kernel before it ends (it
+ *       waits for its predecessor before it reads or writes memory); 0: plain
+ *       stream order (-1 = default, 6: the scan and stream kernels);
  *   "bp128.blocklane_store" = 0 (default: through shared memory, coalesced
  *       16-byte stores), 1 (32-byte stores per lane), 2 (16-byte stores per
  *       lane): output path of the two-pass decoders;

@@ -269,6 +269,10 @@ icx_status icx_set_tuning(const char* key, int value) {
         icx::set_fastpfor_stream_warps(value);
         return ICX_OK;
     }
+    if (!strcmp(key, "fastpfor.chain_overlap")) {
+        icx::set_fastpfor_chain_overlap(value);
+        return ICX_OK;
+    }
     if (!strcmp(key, "fastpfor.blocklane")) {
         icx::set_fastpfor_blocklane(value);
         return ICX_OK;

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kMetaThreads, 7)
     fastpfor_meta_kernel(const uint8_t* __restrict__ in, size_t in_bytes, size_t n, const uint64_t* __restrict__ index,
                          BlockMeta* __restrict__ meta, uint32_t* __restrict__ pmeta, uint2* __restrict__ umeta,
                          WsHeader* h) {
+    allow_dependents();  // a prepare kernel launched as a dependent may be scheduled now
     meta_page<ICX_FMT_PAPER>(in, in_bytes, n, index, meta, pmeta, umeta, h);
 }
 

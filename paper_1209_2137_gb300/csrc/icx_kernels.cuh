@@ -51,5 +51,6 @@ void set_bp128_blocklane_sumw(int v);
 void set_fastpfor_warps(int w);
 void set_fastpfor_blocklane(int on);
 void set_fastpfor_stream_warps(int w);
+void set_fastpfor_chain_overlap(int v);
 
 }  // namespace icx

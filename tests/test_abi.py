@@ -97,7 +97,7 @@ def test_tuning_keys(lib):
     for key, value in [("bp128.warps_per_cta", 0), ("bp128.l2_prefetch", 1), ("fastpfor.warps_per_cta", 0),
                        ("bp128.blocklane", 1), ("fastpfor.blocklane", -1), ("bp128.blocklane_store", -1),
                        ("bp128.blocklane_ctas", 0), ("bp128.blocklane_lead", 0), ("bp128.blocklane_sum_warps", 0),
-                       ("fastpfor.stream_warps", 0)]:
+                       ("fastpfor.stream_warps", 0), ("fastpfor.chain_overlap", 1)]:
         icx.set_tuning(key, value)
     with pytest.raises(icx.IcxError) as e:
         icx.set_tuning("no.such.key", 1)

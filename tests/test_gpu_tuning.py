@@ -74,6 +74,11 @@ def test_blocklane_variants_match_oracle(streams):
                 if codec == "fastpfor":
                     assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("stream warps", w, delta)
         icx.set_tuning("fastpfor.stream_warps", 0)
+        for overlap in (0, 1, 2, 4, 6, 7):  # the prepare / scan / stream chain: stream order, each boundary, all
+            icx.set_tuning("fastpfor.chain_overlap", overlap)
+            for codec, delta, fmt, enc, idx, want in streams:
+                if codec == "fastpfor":
+                    assert np.array_equal(decode(codec, delta, fmt, enc, idx), want), ("chain overlap", overlap, delta)
         for fp_mode in (2, 1):  # the two SIMD-FastPFOR decoders that take these settings
             icx.set_tuning("fastpfor.blocklane", fp_mode)
             for store in (0, 1, 2):
@@ -121,6 +126,7 @@ def test_blocklane_variants_match_oracle(streams):
         icx.set_tuning("bp128.blocklane", 1)
         icx.set_tuning("fastpfor.blocklane", -1)
         icx.set_tuning("fastpfor.stream_warps", 0)
+        icx.set_tuning("fastpfor.chain_overlap", -1)
         icx.set_tuning("bp128.blocklane_store", -1)
         icx.set_tuning("bp128.blocklane_ctas", 0)
         icx.set_tuning("bp128.blocklane_lead", 0)
