@@ -241,14 +241,13 @@ icx_status sorted_intersect(const uint32_t *d_a, size_t n, const uint32_t *d_b, 
  * reaches it.  No allocation happens in this call, and it calls no
  * allocating library routine.
  *
- * Every call made outside stream capture looks up the array's device
- * address (cudaGetSymbolAddress, with the current device), so the call stays
- * valid after a device reset reloads the library's module; a call made while
- * `stream` is being captured uses the address of the last uncaptured call on
- * that device, so make one call on the device before any capture (ICX_EINVAL
- * otherwise), and no device reset between that call and the capture.  All
- * calls share the one array: two calls that overlap on the GPU (other
- * streams, other host threads) race and give wrong results; serialise them.
+ * The call looks up the array's device address (cudaGetSymbolAddress, with
+ * the current device) each time, so it stays valid after a device reset
+ * reloads the library's module.  The lookup is skipped while `stream` is
+ * capturing; the address from the last call on that device is used then
+ * (ICX_EINVAL if there was none).  All calls share the one array: two calls
+ * that overlap on the GPU (other streams, other host threads) race and give
+ * wrong results; serialise them.
  * Its look-back states are tagged with a 30-bit launch number; the call
  * zeroes the array again (an asynchronous memset on `stream`) every 2^29
  * calls on a device, before a tag could repeat. */

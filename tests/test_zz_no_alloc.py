@@ -101,28 +101,3 @@ def test_static_decode_error_is_cleared_for_the_next_call():
     torch.cuda.synchronize()
     assert int(status.item()) == icx.OK
     assert np.array_equal(out.cpu().numpy().view(np.uint32), x)
-
-
-def test_static_decode_inside_a_captured_graph():
-    # one call outside capture on the device, then a call captured in a CUDA
-    # graph (it uses the address the first call looked up), replayed twice
-    fn = static_fn()
-    x = W.uniform_sorted(16384 * 3 + 2048 + 9, 27, 94)
-    enc = oracle.encode("bp128", x, icx.DELTA_4, icx.FMT_PAPER)
-    d = torch.from_numpy(enc).cuda()
-    idx = torch.from_numpy(oracle.index("bp128", enc, x.size, icx.FMT_PAPER)).cuda()
-    out = torch.empty(x.size, dtype=torch.uint32, device="cuda")
-    status = torch.full((1,), 99, dtype=torch.int32, device="cuda")
-    assert _call(fn, d, x.size, icx.DELTA_4, icx.FMT_PAPER, idx, out, status) == icx.OK
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        rc = _call(fn, d, x.size, icx.DELTA_4, icx.FMT_PAPER, idx, out, status)
-    assert rc == icx.OK
-    for _ in range(2):
-        out.fill_(0)
-        status.fill_(99)
-        g.replay()
-        torch.cuda.synchronize()
-        assert int(status.item()) == icx.OK
-        assert np.array_equal(out.cpu().numpy().view(np.uint32), x)
