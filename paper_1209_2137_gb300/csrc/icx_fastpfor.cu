@@ -3,13 +3,17 @@
 //
 // The byte array of a page (per block b, maxbits and, for blocks with
 // exceptions, the count c and c positions) has variable-length records, so
-// finding block k's record needs the records before it.  The decode is
-// therefore two launches:
+// finding block k's record needs the records before it.  Every decode
+// therefore starts with the page parse:
 //  1. fastpfor_meta_kernel -- one CTA per page finds the record starts of
 //     its byte array (jump tables + an 8-record chain, see below) and writes
 //     a fixed 16-byte record per block (packed offset, positions offset,
 //     exception cursor, b, d, c) plus the page-relative offsets of the 32
-//     exception arrays;
+//     exception arrays.
+// With a stride (D1, D4) the SIMD layout then goes, by default, through the
+// prepare / tile-scan / stream kernels of icx_fp_prep.cu.  This file holds
+// the tile decoders that serve the rest (no delta, the scalar and Simple-8b
+// layouts, and fastpfor.blocklane = 0):
 //  2. fastpfor_decode_kernel (no delta, D1) or fastpfor_decode_pipe_kernel
 //     (D4) -- units of 16 blocks exactly like the SIMD-BP128 decoder: one
 //     bulk copy of the unit's packed low bits into

@@ -1,29 +1,36 @@
-// SIMD-FastPFOR decoding fused with differential decoding (Sec. 5, Sec. 6.2)
-// in two kernels: one that prepares every block, one that streams the
-// decoded integers out.
+// SIMD-FastPFOR decoding fused with differential decoding (Sec. 5, Sec. 6.2):
+// the kernels that follow the page parse (fastpfor_meta_kernel, which writes
+// one record per block: packed offset, positions offset, exception cursor,
+// b, d, c).
 //
-//  1. fastpfor_prep_kernel, one CTA per page (in the order the CTAs start):
-//     parses the page's byte array (the record of every block), then per
-//     block (one thread each) sums its integers -- the low parts by walking
+//  1. fastpfor_prep_kernel, one CTA per tile of 256 blocks (half a page), one
+//     thread per block: sums the block's integers -- the low parts by walking
 //     its packed rows, plus high << b for each exception -- and leaves the
-//     block's exceptions for the second kernel in the pair's own output
+//     block's exceptions for the stream kernel in its pair's own output
 //     region: one 32-bit entry (position | high << 8) per exception, in
 //     position order.  A block whose exceptions cannot be written so (high
 //     parts wider than 24 bits, positions out of order or repeated) is
-//     decoded there completely instead, as its 128 differences (Sec. 5:
-//     every exception OR-ed in as high << b, in stream order).  The block
-//     sums are scanned across the page and across pages (decoupled
-//     look-back), and each block's carry (its exclusive prefix, Sec. 3) is
-//     written with its packed offset and entry offset.  The CTA of the last
-//     page also decodes the Variable Byte tail (Sec. 2.4).
-//  2. fastpfor_stream_kernel, persistent warps, one pair of 32 blocks per
+//     written there whole instead, as its 128 differences (every exception
+//     OR-ed in as high << b, in stream order); a pair whose packed bits and
+//     entries would not fit the stream kernel's staging slot is left as
+//     differences in its own output.  A CTA scan gives each block its carry
+//     inside the tile (written with its packed offset and entry offset) and
+//     the tile's sum.
+//  2. fastpfor_tile_scan_kernel, one CTA: turns the tile sums into tile
+//     prefixes (Sec. 3) and decodes the Variable Byte tail (Sec. 2.4).
+//  3. fastpfor_stream_kernel, persistent warps, one pair of 32 blocks per
 //     step: one bulk copy of the pair's packed low bits and one of its
 //     entries (or complete blocks) from its output region into shared
-//     memory; then lane L walks block L's fields from its carry as the
-//     SIMD-BP128 decoder does, ORs each entry into its field just before
-//     that field is emitted, and the fields are written through the
-//     restaging buffer.  A pair's output region is read before it is
-//     written, and by the warp that writes it.
+//     memory; then lane L walks block L's fields from its carry plus the
+//     tile prefix as the SIMD-BP128 decoder does, ORs each entry into its
+//     field just before that field is emitted, and the fields are written
+//     through the restaging buffer.  A pair's output region is read before
+//     it is written, and by the warp that writes it.
+//
+// No kernel waits on another CTA.  The scan and stream kernels are launched
+// as programmatic dependents of the kernel before them: they may be
+// scheduled while it drains and wait for it (grid_dependency_wait) before
+// their first memory access.
 #include <cstddef>
 
 #include "icx_blocklane.cuh"
